@@ -1,0 +1,398 @@
+"""Throughput benchmark of the synchronous-step ACS tour construction.
+
+Workload (the paper-scale plain ACS): two clustered instances, n=1002 and
+n=2392 (20 Gaussian clusters, sigma=300, in [0,10000]^2, EUC_2D), m=128 ants,
+32-NN candidate lists, beta=2, q0=0.9, rho=xi=0.1, each run once on the FP32
+pheromone matrix and once on the selective pheromone memory (s=8): four
+independent colonies. One bench step = one full ACS iteration (Alg. 1) of all
+four colonies; the matrix and SPM contexts run concurrently on two streams.
+
+Metric: ant-steps/s = sum over colonies of m*(n-1) per iteration / step time.
+L2 is flushed (256 MiB write) between timed steps, outside the timed events.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload: each step is one oracle iteration of one of the four
+colonies in rotation.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZES = [1002, 2392]
+M = 128
+CL = 32
+MEM_NAMES = {0: "matrix", 1: "spm"}
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def workload_config():
+    return {
+        "workload": "plain ACS at paper scale: n=1002 and n=2392 clustered (20 clusters, "
+                    "sigma=300, [0,10000]^2, EUC_2D), m=128, 32-NN, beta=2, q0=0.9, "
+                    "rho=xi=0.1, FP32 matrix and SPM s=8 (4 colonies)",
+        "instances": SIZES,
+        "m": M,
+        "cl": CL,
+        "memories": ["matrix", "spm_s8"],
+        "step": "one ACS iteration of all 4 colonies",
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+def make_coords(seed_offset=0):
+    from paper_1605_02669_gb300 import instances
+
+    return [instances.clustered(n, seed=2 + seed_offset) for n in SIZES]
+
+
+def ant_steps_per_iter():
+    return 2 * sum(M * (n - 1) for n in SIZES)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_PEAK_FALLBACK}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def run_reference(args, rank, world):
+    """CPU oracle, single thread, bounded sample (one colony-iteration per step)."""
+    import oracle
+
+    if rank != 0:
+        return None
+    coords = make_coords()
+    colonies = []
+    for mem in (0, 1):
+        for xy in coords:
+            p = oracle.make_params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem,
+                                   spm_slots=8, seed=1)
+            colonies.append(oracle.Colony(xy, p))
+    units = [M * (c.n - 1) for c in colonies]
+    for i in range(args.warmup):
+        colonies[i % 4].run(1)
+    t_total, u_total = 0.0, 0
+    for i in range(args.steps):
+        c = colonies[i % 4]
+        t0 = time.perf_counter()
+        c.run(1)
+        t_total += time.perf_counter() - t0
+        u_total += units[i % 4]
+    value = u_total / t_total
+    sample = ("one single-thread oracle iteration per step, rotating over the 4 colonies "
+              "(n=1002/2392 x matrix/SPM, m=128)")
+    return {
+        "impl": "reference",
+        "metric": "ant-steps/s in tour construction",
+        "value": value,
+        "unit": "ant-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_total / max(args.steps, 1),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "ant-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline_leg(seconds_budget=15.0):
+    """The oracle as it stands, one thread, on a bounded sample of the workload."""
+    import oracle
+
+    coords = make_coords()
+    done_units, t_total = 0, 0.0
+    iters = {}
+    for mem in (0, 1):
+        for xy in coords:
+            p = oracle.make_params(m=M, cl=CL, q0=0.9, memory=mem, spm_slots=8, seed=1)
+            c = oracle.Colony(xy, p)
+            t0 = time.perf_counter()
+            c.run(1)
+            dt = time.perf_counter() - t0
+            t_total += dt
+            done_units += M * (xy.shape[0] - 1)
+            iters["%s_n%d" % (MEM_NAMES[mem], xy.shape[0])] = 1
+            c.close()
+            if t_total > seconds_budget:
+                break
+    return {"value": done_units / t_total, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "one oracle iteration of each colony (n=1002/2392 x matrix/SPM, "
+                      "m=128), single thread, %.1f s" % t_total}
+
+
+def algorithmic_bytes(n, m, fallbacks, spm):
+    """Bytes one iteration of one colony must touch (per ant-step, plus the
+    full-scan fallback): candidate row (index 128 B + weight 128 B), the
+    pheromone of the candidates (matrix gather 128 B, or the SPM record
+    s*8+4 = 68 B), the local update (matrix: 2 entries written, 8 B read+write
+    of one edge = 16 B; SPM: two record read-modify-writes, 2*68 B); each
+    fallback selection reads the pheromone row (4n B, or the record) and the
+    coordinates (8n B)."""
+    steps = m * (n - 1)
+    if spm:
+        per = 256 + 68 + 136
+        fb = fallbacks * (8 * n + 68)
+    else:
+        per = 256 + 128 + 16
+        fb = fallbacks * 12 * n
+    return steps * per + fb
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1605_02669_gb300 import acs
+
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    coords = make_coords(seed_offset=rank)
+    xy = np.concatenate(coords).astype(np.int32)
+    off = np.zeros(len(coords) + 1, np.int64)
+    off[1:] = np.cumsum([c.shape[0] for c in coords])
+    sA = torch.cuda.Stream()
+    sB = torch.cuda.Stream()
+    ctxs = []
+    for mem, st in ((acs.ACS_MEM_MATRIX, sA), (acs.ACS_MEM_SPM, sB)):
+        p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
+                       seed=1 + rank)
+        col = acs.Colony(xy, p, offsets=off)
+        col.set_stream(sA.cuda_stream if st is sA else sB.cuda_stream)
+        ctxs.append((col, st))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(record=None):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        evm0 = torch.cuda.Event(enable_timing=True)
+        evm1 = torch.cuda.Event(enable_timing=True)
+        evb = torch.cuda.Event()
+        ev0.record(sA)
+        sB.wait_event(ev0)
+        evm0.record(sA)
+        ctxs[0][0].run(1)
+        evm1.record(sA)
+        ctxs[1][0].run(1)
+        evb.record(sB)
+        sA.wait_event(evb)
+        ev1.record(sA)
+        return ev0, ev1, evm0, evm1
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        torch.cuda.synchronize()
+        step()
+    torch.cuda.synchronize()
+    fb0 = [ctxs[0][0].stats(b)[0] for b in range(len(SIZES))]
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    events = []
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        events.append(step())
+        launches += acs.acs_last_launch_count(ctxs[0][0].ctx) + acs.acs_last_launch_count(ctxs[1][0].ctx)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [e0.elapsed_time(e1) for e0, e1, _, _ in events]
+    mat_ms = [m0.elapsed_time(m1) for _, _, m0, m1 in events]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    fb1 = [ctxs[0][0].stats(b)[0] for b in range(len(SIZES))]
+    units = ant_steps_per_iter() * args.steps * world
+    value = units / (total_ms / 1000.0)
+
+    # dominant kernel: the matrix construct launch (both matrix instances)
+    fb_per_launch = [(b - a) / args.steps for a, b in zip(fb0, fb1)]
+    bytes_launch = sum(algorithmic_bytes(n, M, f, False) for n, f in zip(SIZES, fb_per_launch))
+    mat_avg_s = float(np.mean(mat_ms)) / 1000.0
+    achieved = bytes_launch / mat_avg_s / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+
+    # end to end through the public API: host coordinates in, best tour out
+    # every iteration (pinned host buffers not needed by the C ABI: it copies)
+    e2e = None
+    if rank == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cols = []
+        for mem in (acs.ACS_MEM_MATRIX, acs.ACS_MEM_SPM):
+            p = acs.params(m=M, cl=CL, memory=mem, spm_slots=8, seed=1)
+            cols.append(acs.Colony(xy, p, offsets=off))
+        d2h = 0
+        for _ in range(args.steps):
+            for c in cols:
+                c.run(1)
+            for c in cols:
+                for b in range(len(SIZES)):
+                    t, L = c.best(b)
+                    d2h += t.nbytes + 8
+        t1 = time.perf_counter()
+        for c in cols:
+            c.close()
+        e2e = {"value": ant_steps_per_iter() * args.steps / (t1 - t0), "unit": "ant-steps/s",
+               "h2d_bytes_per_step": int(2 * xy.nbytes / args.steps + 2 * off.nbytes / args.steps),
+               "d2h_bytes_per_step": int(d2h / args.steps),
+               "includes": "context creation from host coordinates (candidate lists, "
+                           "nearest-neighbour tour, pheromone init) and a best-tour read "
+                           "after every iteration"}
+
+    if rank != 0:
+        return None
+    cpu = None if args.no_cpu_baseline else cpu_baseline_leg()
+    return {
+        "metric": "ant-steps/s in tour construction",
+        "value": value,
+        "unit": "ant-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(),
+        "iterations_per_s": 1000.0 * args.steps / total_ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "construct_kernel<8,false> (matrix, n=1002+2392 in one launch)",
+                     "peak_kind": peak_kind,
+                     "kernel_ms": float(np.mean(mat_ms))},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "fallback_rate": float(sum(fb_per_launch) / (M * sum(n - 1 for n in SIZES))),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+/*
+ * acs.h -- C ABI of libacs, a GB300 (sm_103a) implementation of the
+ * synchronous-step Ant Colony System for the symmetric TSP, after
+ * Skinderowicz, "The GPU-based Parallel Ant Colony System" (JPDC 2016).
+ *
+ * Problem (Sec. 3): a complete graph on n nodes with integer coordinates;
+ * the cost d_ij is the EUC_2D distance nint(sqrt(dx^2+dy^2)); the output is a
+ * short Hamiltonian cycle. One "colony" (instance) is solved by m ants per
+ * iteration (Alg. 1): each ant starts at a random node and extends its tour
+ * step by step with the pseudo-random-proportional rule (Eq. 1-2, Alg. 2)
+ * over a candidate list of the cl nearest neighbours, falling back to the
+ * best unvisited node when the list is exhausted; every step's edges get the
+ * local pheromone update (Eq. 3); after the tours are closed and evaluated
+ * the best-so-far tour gets the global update (eq. global_update). The
+ * pheromone memory is either the n x n FP32 matrix or the selective
+ * pheromone memory (Sec. 3.2, Alg. 3).
+ *
+ * Determinism contract: for a given (coordinates, parameters, seed,
+ * instance index) every call sequence yields bit-identical tours, tour
+ * lengths and pheromone state, equal to the CPU oracle shipped with the tests.
+ * All ants of a step read the pheromone state left by the previous step; an
+ * undirected edge taken by k ants in one step gets one local update with
+ * factor (1-xi)^k (tau <- tau0 + P[k]*(tau - tau0), P[k] an FP32 table built
+ * by repeated multiplication). Randomness is Philox4x32-10 keyed by the seed,
+ * counter (iteration, ant, step, instance).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named coords, tour_out, ... are HOST pointers unless the name
+ *     says dev_. Inputs are copied; the caller keeps ownership.
+ *   - Output buffers are caller-allocated host memory. Calls that return data
+ *     synchronise the context's stream first.
+ *   - The context owns all device memory it allocates; acs_destroy frees it.
+ *   - Every call returns an acs_status and never aborts. On ACS_EINVAL /
+ *     ACS_ENOMEM the context is unchanged. After ACS_ECUDA or ACS_ETIMEOUT
+ *     the context is poisoned: later calls on it return ACS_ESTATE.
+ *   - Limits: 3 <= n <= 65536 per instance; coordinates in [0, 2^20);
+ *     1 <= m <= 1024; 1 <= cl <= 32 (clamped to n-1); 0 <= beta <= 8;
+ *     1 <= spm_slots <= 32.
+ *   - A context is not thread-safe; use one host thread per context.
+ */
+#ifndef ACS_H
+#define ACS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ACS_OK = 0,
+    ACS_EINVAL = 1,   /* bad argument; nothing changed */
+    ACS_ENOMEM = 2,   /* device or host allocation failed; nothing changed */
+    ACS_ECUDA = 3,    /* a CUDA call or a kernel failed; context poisoned */
+    ACS_ETIMEOUT = 4, /* a bounded device wait gave up; context poisoned */
+    ACS_ESTATE = 5    /* context poisoned earlier, or no result yet */
+} acs_status;
+
+typedef enum { ACS_MEM_MATRIX = 0, ACS_MEM_SPM = 1 } acs_memory;
+
+/* Parameters shared by all instances of a context. Names follow the ACS
+ * literature; note the paper writes the local evaporation as rho (Eq. 3) and
+ * the global one as alpha (eq. global_update). */
+typedef struct {
+    int32_t  m;            /* ants per instance, 1..1024 */
+    int32_t  cl;           /* candidate-list width, 1..32, clamped to n-1 */
+    int32_t  beta;         /* integer exponent of eta = 1/max(d,1), 0..8 */
+    float    q0;           /* exploit iff q < q0, q uniform on [0,1); [0,1] */
+    float    rho;          /* global evaporation, (0,1) (paper's alpha) */
+    float    xi;           /* local evaporation, (0,1) (paper's rho, Eq. 3) */
+    int32_t  memory;       /* acs_memory */
+    int32_t  spm_slots;    /* s, trails per node in the SPM, 1..32 */
+    int32_t  local_period; /* local update only at steps s with s % k == 0
+                              (Sec. 4, "Limiting the number of local
+                              pheromone updates"); 1 = every step */
+    int32_t  flags;        /* reserved, must be 0 */
+    uint64_t seed;         /* Philox key */
+} acs_params;
+
+typedef struct acs_ctx acs_ctx;
+
+/* One instance. coords: host int32 [n][2] (x, y). Instance index 0.
+ * Builds the candidate lists (cl nearest neighbours sorted by distance, then
+ * index), the heuristic table w = 1/max(d,1)^beta, the nearest-neighbour tour
+ * from node 0 and tau0 = 1/(n*L_nn), and initialises the pheromone memory. */
+acs_status acs_create(const int32_t* coords, int32_t n, const acs_params* p,
+                      acs_ctx** out);
+
+/* B independent instances solved together (one persistent launch per
+ * iteration). coords: host int32 [sum n_b][2]; offsets: host int64 [B+1],
+ * offsets[0]=0, instance b owns nodes offsets[b]..offsets[b+1]-1. Instance b
+ * uses Philox counter word 3 = b. */
+acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets,
+                            int32_t B, const acs_params* p, acs_ctx** out);
+
+/* Run later work on this CUDA stream (a cudaStream_t; NULL = legacy default).
+ * The CUDA graph captured for one iteration is rebuilt on the next run. */
+acs_status acs_set_stream(acs_ctx* ctx, void* cuda_stream);
+
+/* Run `iters` full iterations of Alg. 1 on every instance (stream-ordered,
+ * asynchronous; replays a captured CUDA graph of one iteration). */
+acs_status acs_run_iterations(acs_ctx* ctx, int32_t iters);
+
+/* Best-so-far tour (n node indices, 0-based, starting at the ant's first
+ * node, closing implicitly) and its length. ACS_ESTATE before the first
+ * iteration. */
+acs_status acs_best_tour(acs_ctx* ctx, int32_t instance, int32_t* tour_out,
+                         int64_t* len_out);
+
+/* Tours [m][n] and lengths [m] of the last iteration (either may be NULL). */
+acs_status acs_get_tours(acs_ctx* ctx, int32_t instance, int32_t* tours,
+                         int64_t* lens);
+
+/* Pheromone state. Matrix: tau_or_val = float [n][n]; spm_idx/spm_tail
+ * ignored. SPM: tau_or_val = float [n][s] trail values, spm_idx = int32
+ * [n][s] neighbour per slot (-1 = empty), spm_tail = int32 [n] most recently
+ * written slot. NULL outputs are skipped. */
+acs_status acs_get_pheromone(acs_ctx* ctx, int32_t instance, float* tau_or_val,
+                             int32_t* spm_idx, int32_t* spm_tail);
+
+/* Set-up tables: nn int32 [n][cl_eff], w float [n][cl_eff], tau0, L_nn and
+ * the effective candidate width (any output may be NULL). */
+acs_status acs_get_setup(acs_ctx* ctx, int32_t instance, int32_t* nn, float* w,
+                         float* tau0, int64_t* L_nn, int32_t* cl_eff);
+
+/* Counters accumulated over all iterations of one instance:
+ * out[0] full-scan fallback selections, out[1] all selections,
+ * out[2] SPM hits, out[3] SPM misses (Sec. 3.2, Fig. spm-hit-ratio). */
+acs_status acs_get_stats(acs_ctx* ctx, int32_t instance, int64_t out[4]);
+
+/* Iterations completed (same for every instance of the context). */
+int64_t acs_iteration(const acs_ctx* ctx);
+int32_t acs_num_instances(const acs_ctx* ctx);
+int32_t acs_instance_size(const acs_ctx* ctx, int32_t instance);
+
+/* Kernel launches made by the last acs_run_iterations call (for accounting). */
+int64_t acs_last_launch_count(const acs_ctx* ctx);
+
+const char* acs_strerror(acs_status s);
+void acs_destroy(acs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

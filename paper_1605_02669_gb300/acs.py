@@ -1,0 +1,250 @@
+"""Thin ctypes binding of libacs (include/acs.h): argument marshalling only.
+
+Every step of the colony runs in the CUDA library; there is no CPU path. If
+libacs.so is missing or cannot be loaded, importing the library raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libacs.so")
+
+ACS_OK, ACS_EINVAL, ACS_ENOMEM, ACS_ECUDA, ACS_ETIMEOUT, ACS_ESTATE = range(6)
+ACS_MEM_MATRIX, ACS_MEM_SPM = 0, 1
+
+
+class AcsError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, strerror(status), status))
+
+
+class acs_params(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int32),
+        ("cl", ctypes.c_int32),
+        ("beta", ctypes.c_int32),
+        ("q0", ctypes.c_float),
+        ("rho", ctypes.c_float),
+        ("xi", ctypes.c_float),
+        ("memory", ctypes.c_int32),
+        ("spm_slots", ctypes.c_int32),
+        ("local_period", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+def params(m=32, cl=32, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=ACS_MEM_MATRIX,
+           spm_slots=8, local_period=1, seed=1):
+    return acs_params(m, cl, beta, q0, rho, xi, memory, spm_slots, local_period, 0, seed)
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+def load():
+    """Load libacs.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libacs.so not built at %s; run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    L.acs_create.argtypes = [_vp, _i32, P(acs_params), P(_vp)]
+    L.acs_create_batch.argtypes = [_vp, _vp, _i32, P(acs_params), P(_vp)]
+    L.acs_set_stream.argtypes = [_vp, _vp]
+    L.acs_run_iterations.argtypes = [_vp, _i32]
+    L.acs_best_tour.argtypes = [_vp, _i32, _vp, _vp]
+    L.acs_get_tours.argtypes = [_vp, _i32, _vp, _vp]
+    L.acs_get_pheromone.argtypes = [_vp, _i32, _vp, _vp, _vp]
+    L.acs_get_setup.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp]
+    L.acs_get_stats.argtypes = [_vp, _i32, _vp]
+    L.acs_iteration.argtypes = [_vp]
+    L.acs_iteration.restype = _i64
+    L.acs_num_instances.argtypes = [_vp]
+    L.acs_num_instances.restype = _i32
+    L.acs_instance_size.argtypes = [_vp, _i32]
+    L.acs_instance_size.restype = _i32
+    L.acs_last_launch_count.argtypes = [_vp]
+    L.acs_last_launch_count.restype = _i64
+    L.acs_strerror.argtypes = [ctypes.c_int]
+    L.acs_strerror.restype = ctypes.c_char_p
+    L.acs_destroy.argtypes = [_vp]
+    L.acs_destroy.restype = None
+    for name in ["acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
+                 "acs_best_tour", "acs_get_tours", "acs_get_pheromone", "acs_get_setup",
+                 "acs_get_stats"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def strerror(status):
+    try:
+        return load().acs_strerror(status).decode()
+    except ImportError:
+        return "status %d" % status
+
+
+def _check(rc, what):
+    if rc != ACS_OK:
+        raise AcsError(rc, what)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_vp)
+
+
+# ---- the C ABI under the same names -------------------------------------------------
+
+def acs_create(coords, p):
+    coords = np.ascontiguousarray(coords, np.int32)
+    h = _vp()
+    _check(load().acs_create(_ptr(coords), coords.shape[0], ctypes.byref(p), ctypes.byref(h)),
+           "acs_create")
+    return h
+
+
+def acs_create_batch(coords, offsets, p):
+    coords = np.ascontiguousarray(coords, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    h = _vp()
+    _check(load().acs_create_batch(_ptr(coords), _ptr(offsets), offsets.shape[0] - 1,
+                                   ctypes.byref(p), ctypes.byref(h)), "acs_create_batch")
+    return h
+
+
+def acs_set_stream(ctx, stream_handle):
+    _check(load().acs_set_stream(ctx, _vp(stream_handle or 0)), "acs_set_stream")
+
+
+def acs_run_iterations(ctx, iters):
+    _check(load().acs_run_iterations(ctx, int(iters)), "acs_run_iterations")
+
+
+def acs_best_tour(ctx, instance, n):
+    t = np.zeros(n, np.int32)
+    L = np.zeros(1, np.int64)
+    _check(load().acs_best_tour(ctx, instance, _ptr(t), _ptr(L)), "acs_best_tour")
+    return t, int(L[0])
+
+
+def acs_get_tours(ctx, instance, m, n):
+    t = np.zeros((m, n), np.int32)
+    L = np.zeros(m, np.int64)
+    _check(load().acs_get_tours(ctx, instance, _ptr(t), _ptr(L)), "acs_get_tours")
+    return t, L
+
+
+def acs_get_pheromone(ctx, instance, n, memory, s=0):
+    if memory == ACS_MEM_MATRIX:
+        tau = np.zeros((n, n), np.float32)
+        _check(load().acs_get_pheromone(ctx, instance, _ptr(tau), None, None), "acs_get_pheromone")
+        return tau
+    val = np.zeros((n, s), np.float32)
+    idx = np.zeros((n, s), np.int32)
+    tail = np.zeros(n, np.int32)
+    _check(load().acs_get_pheromone(ctx, instance, _ptr(val), _ptr(idx), _ptr(tail)),
+           "acs_get_pheromone")
+    return val, idx, tail
+
+
+def acs_get_setup(ctx, instance, n, cl_max):
+    cl = np.zeros(1, np.int32)
+    tau0 = np.zeros(1, np.float32)
+    lnn = np.zeros(1, np.int64)
+    _check(load().acs_get_setup(ctx, instance, None, None, _ptr(tau0), _ptr(lnn), _ptr(cl)),
+           "acs_get_setup")
+    c = int(cl[0])
+    nn = np.zeros((n, c), np.int32)
+    w = np.zeros((n, c), np.float32)
+    _check(load().acs_get_setup(ctx, instance, _ptr(nn), _ptr(w), None, None, None),
+           "acs_get_setup")
+    return nn, w, np.float32(tau0[0]), int(lnn[0])
+
+
+def acs_get_stats(ctx, instance):
+    out = np.zeros(4, np.int64)
+    _check(load().acs_get_stats(ctx, instance, _ptr(out)), "acs_get_stats")
+    return tuple(int(x) for x in out)
+
+
+def acs_iteration(ctx):
+    return int(load().acs_iteration(ctx))
+
+
+def acs_num_instances(ctx):
+    return int(load().acs_num_instances(ctx))
+
+
+def acs_instance_size(ctx, instance):
+    return int(load().acs_instance_size(ctx, instance))
+
+
+def acs_last_launch_count(ctx):
+    return int(load().acs_last_launch_count(ctx))
+
+
+def acs_destroy(ctx):
+    if ctx:
+        load().acs_destroy(ctx)
+
+
+# ---- convenience wrapper ---------------------------------------------------------
+
+class Colony:
+    """One context (one instance, or a batch) with numpy in/out."""
+
+    def __init__(self, coords, p, offsets=None):
+        self.p = p
+        coords = np.ascontiguousarray(coords, np.int32)
+        if offsets is None:
+            self.ctx = acs_create(coords, p)
+            self.sizes = [coords.shape[0]]
+        else:
+            self.ctx = acs_create_batch(coords, offsets, p)
+            off = np.asarray(offsets, np.int64)
+            self.sizes = [int(x) for x in np.diff(off)]
+
+    def run(self, iters):
+        acs_run_iterations(self.ctx, iters)
+
+    def set_stream(self, handle):
+        acs_set_stream(self.ctx, handle)
+
+    @property
+    def iteration(self):
+        return acs_iteration(self.ctx)
+
+    def best(self, b=0):
+        return acs_best_tour(self.ctx, b, self.sizes[b])
+
+    def tours(self, b=0):
+        return acs_get_tours(self.ctx, b, self.p.m, self.sizes[b])
+
+    def pheromone(self, b=0):
+        return acs_get_pheromone(self.ctx, b, self.sizes[b], self.p.memory, self.p.spm_slots)
+
+    def setup(self, b=0):
+        return acs_get_setup(self.ctx, b, self.sizes[b], 32)
+
+    def stats(self, b=0):
+        return acs_get_stats(self.ctx, b)
+
+    def close(self):
+        if self.ctx:
+            acs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,641 @@
+// acs_api.cu -- host side of libacs: the C ABI of include/acs.h, the set-up
+// kernels (candidate lists, nearest-neighbour tour, pheromone initialisation)
+// and the per-iteration CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "acs.h"
+#include "acs_device.cuh"
+#include "acs_internal.cuh"
+
+namespace acs {
+cudaError_t prepare_construct(int tpa, bool spm, size_t smem);
+cudaError_t launch_construct(const ConstructArgs& A, int tpa, bool spm, int grid, int block,
+                             size_t smem, cudaStream_t stream);
+int construct_occupancy(int tpa, bool spm, int block, size_t smem);
+}  // namespace acs
+
+using namespace acs;
+
+// ------------------------------------------------------------------ kernels
+
+// Candidate lists (Sec. 3, Alg. 2): one warp per node c selects the cl
+// smallest keys (d_cj, j) in cl rounds of a warp-wide minimum above the
+// previous key; rows are padded to 32 with -1 / 0.
+__global__ void knn_kernel(const InstDesc* desc, const int32_t* xy, int32_t* nn, float* w, int beta)
+{
+    const InstDesc D = desc[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= D.n) return;
+    const int2* p = reinterpret_cast<const int2*>(xy) + D.xy_off;
+    const int2 pc = p[c];
+    int32_t* nrow = nn + 32 * (D.row_off + c);
+    float* wrow = w + 32 * (D.row_off + c);
+    unsigned long long prev = 0ull;
+    for (int r = 0; r < 32; ++r) {
+        if (r >= D.cl) {
+            if (lane == 0) { nrow[r] = -1; wrow[r] = 0.0f; }
+            continue;
+        }
+        unsigned long long bk = ~0ull;
+        for (int j = lane; j < D.n; j += 32) {
+            if (j == c) continue;
+            const unsigned long long key = ((unsigned long long)euc2d(pc, p[j]) << 32) | (uint32_t)j;
+            if ((r == 0 || key > prev) && key < bk) bk = key;
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, bk, off);
+            bk = o < bk ? o : bk;
+        }
+        prev = bk;
+        if (lane == 0) {
+            nrow[r] = (int32_t)(bk & 0xffffffffull);
+            wrow[r] = heuristic((int32_t)(bk >> 32), beta);
+        }
+    }
+}
+
+// Nearest-neighbour tour from node 0 (ties -> lowest index), one CTA per
+// instance; sets tau0 = (float)(1/((double)n * L_nn)).
+__global__ void nn_tour_kernel(InstDesc* desc, const int32_t* xy, int64_t* L_out)
+{
+    extern __shared__ uint32_t vis[];
+    __shared__ unsigned long long red[32];
+    __shared__ int s_cur;
+    InstDesc* D = desc + blockIdx.x;
+    const int n = D->n;
+    const int W = (n + 31) >> 5;
+    const int2* p = reinterpret_cast<const int2*>(xy) + D->xy_off;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) vis[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) { vis[0] = 1u; s_cur = 0; }
+    __syncthreads();
+    long long L = 0;
+    for (int step = 1; step < n; ++step) {
+        const int cur = s_cur;
+        const int2 pc = p[cur];
+        unsigned long long bk = ~0ull;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            if ((vis[j >> 5] >> (j & 31)) & 1u) continue;
+            const unsigned long long key = ((unsigned long long)euc2d(pc, p[j]) << 32) | (uint32_t)j;
+            bk = key < bk ? key : bk;
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, bk, off);
+            bk = o < bk ? o : bk;
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bk;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : ~0ull;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+                v = o < v ? o : v;
+            }
+            if (threadIdx.x == 0) {
+                const int nx = (int)(v & 0xffffffffull);
+                L += (long long)(v >> 32);
+                vis[nx >> 5] |= 1u << (nx & 31);
+                s_cur = nx;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        L += euc2d(p[s_cur], p[0]);
+        L_out[blockIdx.x] = L;
+        D->tau0 = __double2float_rn(1.0 / ((double)n * (double)L));
+    }
+}
+
+__global__ void init_matrix_kernel(const InstDesc* desc, float* tau)
+{
+    const InstDesc D = desc[blockIdx.y];
+    const size_t total = (size_t)D.n * D.n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x)
+        tau[D.tau_off + i] = D.tau0;
+}
+
+__global__ void init_spm_kernel(const InstDesc* desc, int32_t* idx, float* val, int32_t* tail, int s)
+{
+    const InstDesc D = desc[blockIdx.y];
+    const size_t total = (size_t)D.n * s;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        idx[D.tau_off + i] = -1;
+        val[D.tau_off + i] = 0.0f;
+    }
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)D.n;
+         i += (size_t)gridDim.x * blockDim.x)
+        tail[D.node_off + i] = s - 1;
+}
+
+// ------------------------------------------------------------------ context
+
+struct acs_ctx {
+    int B = 0;
+    acs_params p{};
+    int m = 0, s = 0;
+    std::vector<int32_t> n, cl;
+    std::vector<InstDesc> desc_h;
+    int max_n = 0;
+    // device memory
+    InstDesc* d_desc = nullptr;
+    int32_t* d_order = nullptr;
+    int32_t* d_xy = nullptr;
+    int32_t* d_nn = nullptr;
+    float* d_w = nullptr;
+    float* d_tau = nullptr;
+    int32_t* d_spm_idx = nullptr;
+    int32_t* d_spm_tail = nullptr;
+    int32_t* d_tours = nullptr;
+    int64_t* d_lens = nullptr;
+    int32_t* d_best = nullptr;
+    int64_t* d_best_len = nullptr;
+    int64_t* d_iter = nullptr;
+    unsigned long long* d_stats = nullptr;
+    uint32_t* d_vis = nullptr;
+    float* d_P = nullptr;
+    int32_t* d_status = nullptr;
+    int64_t* d_Lnn = nullptr;
+    std::vector<void*> allocs;
+    // execution
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ConstructArgs args{};
+    int tpa = 8, grid = 1, block = 256;
+    size_t smem = 0;
+    int64_t iteration = 0;
+    bool poisoned = false;
+    int64_t last_launches = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(acs_ctx* c, T** p, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+}
+
+void free_all(acs_ctx* c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    for (void* q : c->allocs) cudaFree(q);
+    c->allocs.clear();
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    c->own_stream = nullptr;
+}
+
+acs_status validate_params(const acs_params* p)
+{
+    if (!p) return ACS_EINVAL;
+    if (p->m < 1 || p->m > kMaxM) return ACS_EINVAL;
+    if (p->cl < 1 || p->cl > kMaxCl) return ACS_EINVAL;
+    if (p->beta < 0 || p->beta > 8) return ACS_EINVAL;
+    if (!(p->q0 >= 0.0f && p->q0 <= 1.0f)) return ACS_EINVAL;
+    if (!(p->rho > 0.0f && p->rho < 1.0f)) return ACS_EINVAL;
+    if (!(p->xi > 0.0f && p->xi < 1.0f)) return ACS_EINVAL;
+    if (p->memory != ACS_MEM_MATRIX && p->memory != ACS_MEM_SPM) return ACS_EINVAL;
+    if (p->memory == ACS_MEM_SPM && (p->spm_slots < 1 || p->spm_slots > 32)) return ACS_EINVAL;
+    if (p->local_period < 1 || p->flags != 0) return ACS_EINVAL;
+    return ACS_OK;
+}
+
+int next_pow2(int x)
+{
+    int v = 1;
+    while (v < x) v <<= 1;
+    return v;
+}
+
+acs_status fail_cuda(acs_ctx* c, cudaError_t e)
+{
+    if (e != cudaSuccess) {
+        if (c) c->poisoned = true;
+        return ACS_ECUDA;
+    }
+    return ACS_OK;
+}
+
+#define ACS_TRY(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) {                        \
+            cudaGetLastError();                         \
+            return _e;                                  \
+        }                                               \
+    } while (0)
+
+cudaError_t plan_launch(acs_ctx* c)
+{
+    int dev = 0;
+    ACS_TRY(cudaGetDevice(&dev));
+    int max_smem = 0, sms = 0;
+    ACS_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    ACS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int m = c->m;
+    const int H = std::max(64, next_pow2(2 * m));
+    const int H2 = std::max(64, next_pow2(4 * m));
+    const int W = (c->max_n + 31) / 32;
+    const SmemLayout base = smem_layout(m, H, H2, W, c->max_n, false, false);
+    bool vis_smem = base.total + 4ull * m * W <= (unsigned long long)max_smem;
+    bool xy_smem = vis_smem && smem_layout(m, H, H2, W, c->max_n, true, true).total <= (uint32_t)max_smem;
+    const SmemLayout L = smem_layout(m, H, H2, W, c->max_n, vis_smem, xy_smem);
+    if (L.total > (uint32_t)max_smem) return cudaErrorInvalidConfiguration;
+    c->smem = L.total;
+    int block = std::min(1024, std::max(64, m * c->tpa));
+    block = (block + 31) / 32 * 32;
+    if (block < m) block = (m + 31) / 32 * 32;
+    c->block = block;
+    const bool spm = c->p.memory == ACS_MEM_SPM;
+    ACS_TRY(prepare_construct(c->tpa, spm, c->smem));
+    int occ = construct_occupancy(c->tpa, spm, block, c->smem);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    c->grid = std::min(c->B, occ * sms);
+    if (!vis_smem) {
+        size_t words = 0;
+        for (int b = 0; b < c->B; ++b) {
+            c->desc_h[b].vis_off = (int64_t)words;
+            words += (size_t)m * c->desc_h[b].W;
+        }
+        ACS_TRY(dalloc(c, &c->d_vis, words));
+    }
+    ConstructArgs& A = c->args;
+    A.desc = c->d_desc;
+    A.order = c->d_order;
+    A.num_inst = c->B;
+    A.m = m;
+    A.xy = c->d_xy;
+    A.nn = c->d_nn;
+    A.w = c->d_w;
+    A.tau = c->d_tau;
+    A.spm_idx = c->d_spm_idx;
+    A.spm_tail = c->d_spm_tail;
+    A.tours = c->d_tours;
+    A.lens = c->d_lens;
+    A.best = c->d_best;
+    A.best_len = c->d_best_len;
+    A.iteration = c->d_iter;
+    A.stats = c->d_stats;
+    A.vis_global = c->d_vis;
+    A.P = c->d_P;
+    A.status = c->d_status;
+    A.q0 = c->p.q0;
+    A.rho = c->p.rho;
+    A.beta = c->p.beta;
+    A.s = c->s;
+    A.period = c->p.local_period;
+    A.key0 = (uint32_t)(c->p.seed & 0xffffffffull);
+    A.key1 = (uint32_t)(c->p.seed >> 32);
+    A.vis_in_smem = vis_smem ? 1 : 0;
+    A.xy_in_smem = xy_smem ? 1 : 0;
+    A.max_n = c->max_n;
+    A.H = H;
+    A.H2 = H2;
+    return cudaSuccess;
+}
+
+cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
+{
+    const int B = c->B, m = c->m;
+    int64_t total_n = offsets[B];
+    size_t tau_total = 0, tour_total = 0;
+    c->desc_h.resize(B);
+    for (int b = 0; b < B; ++b) {
+        InstDesc& D = c->desc_h[b];
+        const int n = c->n[b];
+        D.n = n;
+        D.cl = c->cl[b];
+        D.W = (n + 31) / 32;
+        D.instance = b;
+        D.xy_off = offsets[b];
+        D.row_off = offsets[b];
+        D.tau_off = (int64_t)tau_total;
+        D.node_off = offsets[b];
+        D.tour_off = (int64_t)tour_total;
+        D.ant_off = (int64_t)b * m;
+        D.vis_off = 0;
+        D.tau0 = 0.0f;
+        D.pad = 0;
+        tau_total += c->p.memory == ACS_MEM_MATRIX ? (size_t)n * n : (size_t)n * c->s;
+        tour_total += (size_t)m * n;
+    }
+    std::vector<int32_t> order(B);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return c->n[a] > c->n[b]; });
+
+    ACS_TRY(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    c->stream = c->own_stream;
+    ACS_TRY(dalloc(c, &c->d_desc, B));
+    ACS_TRY(dalloc(c, &c->d_order, B));
+    ACS_TRY(dalloc(c, &c->d_xy, 2 * (size_t)total_n));
+    ACS_TRY(dalloc(c, &c->d_nn, 32 * (size_t)total_n));
+    ACS_TRY(dalloc(c, &c->d_w, 32 * (size_t)total_n));
+    ACS_TRY(dalloc(c, &c->d_tau, tau_total));
+    if (c->p.memory == ACS_MEM_SPM) {
+        ACS_TRY(dalloc(c, &c->d_spm_idx, tau_total));
+        ACS_TRY(dalloc(c, &c->d_spm_tail, (size_t)total_n));
+    }
+    ACS_TRY(dalloc(c, &c->d_tours, tour_total));
+    ACS_TRY(dalloc(c, &c->d_lens, (size_t)B * m));
+    ACS_TRY(dalloc(c, &c->d_best, (size_t)total_n));
+    ACS_TRY(dalloc(c, &c->d_best_len, B));
+    ACS_TRY(dalloc(c, &c->d_iter, B));
+    ACS_TRY(dalloc(c, &c->d_stats, 4 * (size_t)B));
+    ACS_TRY(dalloc(c, &c->d_P, (size_t)m + 1));
+    ACS_TRY(dalloc(c, &c->d_status, 1));
+    ACS_TRY(dalloc(c, &c->d_Lnn, B));
+
+    // decay table P[0] = 1, P[k] = P[k-1]*(1-xi), FP32
+    std::vector<float> P(m + 1);
+    const float f = 1.0f - c->p.xi;
+    P[0] = 1.0f;
+    for (int k = 1; k <= m; ++k) P[k] = P[k - 1] * f;
+
+    cudaStream_t st = c->stream;
+    ACS_TRY(cudaMemcpyAsync(c->d_xy, coords, sizeof(int32_t) * 2 * total_n, cudaMemcpyHostToDevice, st));
+    ACS_TRY(cudaMemcpyAsync(c->d_desc, c->desc_h.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, st));
+    ACS_TRY(cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
+    ACS_TRY(cudaMemcpyAsync(c->d_P, P.data(), sizeof(float) * (m + 1), cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> big(B, INT64_MAX);
+    ACS_TRY(cudaMemcpyAsync(c->d_best_len, big.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, st));
+    ACS_TRY(cudaMemsetAsync(c->d_iter, 0, sizeof(int64_t) * B, st));
+    ACS_TRY(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * 4 * B, st));
+    ACS_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), st));
+
+    dim3 kg((c->max_n + 7) / 8, B);
+    knn_kernel<<<kg, 256, 0, st>>>(c->d_desc, c->d_xy, c->d_nn, c->d_w, c->p.beta);
+    ACS_TRY(cudaGetLastError());
+    const size_t vis_bytes = sizeof(uint32_t) * ((c->max_n + 31) / 32);
+    nn_tour_kernel<<<B, 1024, vis_bytes, st>>>(c->d_desc, c->d_xy, c->d_Lnn);
+    ACS_TRY(cudaGetLastError());
+    dim3 ig(256, B);
+    if (c->p.memory == ACS_MEM_MATRIX) {
+        init_matrix_kernel<<<ig, 256, 0, st>>>(c->d_desc, c->d_tau);
+    } else {
+        init_spm_kernel<<<ig, 256, 0, st>>>(c->d_desc, c->d_spm_idx, c->d_tau, c->d_spm_tail, c->s);
+    }
+    ACS_TRY(cudaGetLastError());
+    ACS_TRY(cudaMemcpyAsync(c->desc_h.data(), c->d_desc, sizeof(InstDesc) * B, cudaMemcpyDeviceToHost, st));
+    ACS_TRY(cudaStreamSynchronize(st));
+    ACS_TRY(plan_launch(c));
+    // plan_launch may have assigned global visited offsets
+    ACS_TRY(cudaMemcpyAsync(c->d_desc, c->desc_h.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, st));
+    ACS_TRY(cudaStreamSynchronize(st));
+    return cudaSuccess;
+}
+
+acs_status check_device_status(acs_ctx* c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->poisoned = true;
+        return ACS_ECUDA;
+    }
+    int32_t st = 0;
+    e = cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess || st != 0) {
+        c->poisoned = true;
+        return ACS_ECUDA;
+    }
+    return ACS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets, int32_t B,
+                            const acs_params* p, acs_ctx** out)
+{
+    if (!out) return ACS_EINVAL;
+    *out = nullptr;
+    if (!coords || !offsets || B < 1) return ACS_EINVAL;
+    acs_status vs = validate_params(p);
+    if (vs != ACS_OK) return vs;
+    if (offsets[0] != 0) return ACS_EINVAL;
+    int max_n = 0;
+    for (int b = 0; b < B; ++b) {
+        const int64_t n = offsets[b + 1] - offsets[b];
+        if (n < 3 || n > kMaxN) return ACS_EINVAL;
+        max_n = std::max<int>(max_n, (int)n);
+    }
+    const int64_t total = offsets[B];
+    for (int64_t i = 0; i < 2 * total; ++i)
+        if (coords[i] < 0 || coords[i] >= kCoordLimit) return ACS_EINVAL;
+
+    acs_ctx* c = new (std::nothrow) acs_ctx();
+    if (!c) return ACS_ENOMEM;
+    c->B = B;
+    c->p = *p;
+    c->m = p->m;
+    c->s = p->memory == ACS_MEM_SPM ? p->spm_slots : 0;
+    c->max_n = max_n;
+    c->n.resize(B);
+    c->cl.resize(B);
+    for (int b = 0; b < B; ++b) {
+        c->n[b] = (int32_t)(offsets[b + 1] - offsets[b]);
+        c->cl[b] = std::min(p->cl, c->n[b] - 1);
+    }
+    cudaError_t e = build(c, coords, offsets);
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return oom ? ACS_ENOMEM : (e == cudaErrorInvalidConfiguration ? ACS_EINVAL : ACS_ECUDA);
+    }
+    *out = c;
+    return ACS_OK;
+}
+
+acs_status acs_create(const int32_t* coords, int32_t n, const acs_params* p, acs_ctx** out)
+{
+    const int64_t off[2] = {0, (int64_t)n};
+    return acs_create_batch(coords, off, 1, p, out);
+}
+
+acs_status acs_set_stream(acs_ctx* c, void* cuda_stream)
+{
+    if (!c) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+    if (s != c->stream) {
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+        c->stream = s;
+        if (c->exec) cudaGraphExecDestroy(c->exec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->exec = nullptr;
+        c->graph = nullptr;
+    }
+    return ACS_OK;
+}
+
+acs_status acs_run_iterations(acs_ctx* c, int32_t iters)
+{
+    if (!c || iters < 0) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    c->last_launches = 0;
+    if (iters == 0) return ACS_OK;
+    const bool spm = c->p.memory == ACS_MEM_SPM;
+    if (!c->exec) {
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+        cudaError_t le = launch_construct(c->args, c->tpa, spm, c->grid, c->block, c->smem, c->stream);
+        e = cudaStreamEndCapture(c->stream, &c->graph);
+        if (le != cudaSuccess) return fail_cuda(c, le);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+        e = cudaGraphInstantiate(&c->exec, c->graph, 0);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+    }
+    for (int32_t i = 0; i < iters; ++i) {
+        cudaError_t e = cudaGraphLaunch(c->exec, c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+    }
+    c->iteration += iters;
+    c->last_launches = iters;
+    return ACS_OK;
+}
+
+acs_status acs_best_tour(acs_ctx* c, int32_t b, int32_t* tour_out, int64_t* len_out)
+{
+    if (!c || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    acs_status s = check_device_status(c);
+    if (s != ACS_OK) return s;
+    if (c->iteration == 0) return ACS_ESTATE;
+    const InstDesc& D = c->desc_h[b];
+    cudaError_t e = cudaSuccess;
+    if (tour_out) e = cudaMemcpy(tour_out, c->d_best + D.node_off, sizeof(int32_t) * D.n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && len_out) e = cudaMemcpy(len_out, c->d_best_len + b, sizeof(int64_t), cudaMemcpyDeviceToHost);
+    return fail_cuda(c, e);
+}
+
+acs_status acs_get_tours(acs_ctx* c, int32_t b, int32_t* tours, int64_t* lens)
+{
+    if (!c || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    acs_status s = check_device_status(c);
+    if (s != ACS_OK) return s;
+    const InstDesc& D = c->desc_h[b];
+    cudaError_t e = cudaSuccess;
+    if (tours) e = cudaMemcpy(tours, c->d_tours + D.tour_off, sizeof(int32_t) * (size_t)c->m * D.n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && lens) e = cudaMemcpy(lens, c->d_lens + D.ant_off, sizeof(int64_t) * c->m, cudaMemcpyDeviceToHost);
+    return fail_cuda(c, e);
+}
+
+acs_status acs_get_pheromone(acs_ctx* c, int32_t b, float* tau_or_val, int32_t* spm_idx, int32_t* spm_tail)
+{
+    if (!c || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    acs_status s = check_device_status(c);
+    if (s != ACS_OK) return s;
+    const InstDesc& D = c->desc_h[b];
+    cudaError_t e = cudaSuccess;
+    if (c->p.memory == ACS_MEM_MATRIX) {
+        if (tau_or_val) e = cudaMemcpy(tau_or_val, c->d_tau + D.tau_off, sizeof(float) * (size_t)D.n * D.n, cudaMemcpyDeviceToHost);
+    } else {
+        const size_t ns = (size_t)D.n * c->s;
+        if (tau_or_val) e = cudaMemcpy(tau_or_val, c->d_tau + D.tau_off, sizeof(float) * ns, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && spm_idx) e = cudaMemcpy(spm_idx, c->d_spm_idx + D.tau_off, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && spm_tail) e = cudaMemcpy(spm_tail, c->d_spm_tail + D.node_off, sizeof(int32_t) * D.n, cudaMemcpyDeviceToHost);
+    }
+    return fail_cuda(c, e);
+}
+
+acs_status acs_get_setup(acs_ctx* c, int32_t b, int32_t* nn, float* w, float* tau0, int64_t* L_nn, int32_t* cl_eff)
+{
+    if (!c || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    acs_status s = check_device_status(c);
+    if (s != ACS_OK) return s;
+    const InstDesc& D = c->desc_h[b];
+    cudaError_t e = cudaSuccess;
+    if (nn || w) {
+        std::vector<int32_t> nb(32 * (size_t)D.n);
+        std::vector<float> wb(32 * (size_t)D.n);
+        e = cudaMemcpy(nb.data(), c->d_nn + 32 * D.row_off, sizeof(int32_t) * nb.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(wb.data(), c->d_w + 32 * D.row_off, sizeof(float) * wb.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+        for (int i = 0; i < D.n; ++i)
+            for (int k = 0; k < D.cl; ++k) {
+                if (nn) nn[(size_t)i * D.cl + k] = nb[(size_t)i * 32 + k];
+                if (w) w[(size_t)i * D.cl + k] = wb[(size_t)i * 32 + k];
+            }
+    }
+    if (tau0) *tau0 = D.tau0;
+    if (L_nn) e = cudaMemcpy(L_nn, c->d_Lnn + b, sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (cl_eff) *cl_eff = D.cl;
+    return fail_cuda(c, e);
+}
+
+acs_status acs_get_stats(acs_ctx* c, int32_t b, int64_t out[4])
+{
+    if (!c || !out || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    acs_status s = check_device_status(c);
+    if (s != ACS_OK) return s;
+    unsigned long long v[4];
+    cudaError_t e = cudaMemcpy(v, c->d_stats + 4 * (size_t)b, sizeof(v), cudaMemcpyDeviceToHost);
+    for (int i = 0; i < 4; ++i) out[i] = (int64_t)v[i];
+    return fail_cuda(c, e);
+}
+
+int64_t acs_iteration(const acs_ctx* c) { return c ? c->iteration : -1; }
+int32_t acs_num_instances(const acs_ctx* c) { return c ? c->B : -1; }
+int32_t acs_instance_size(const acs_ctx* c, int32_t b)
+{
+    return (c && b >= 0 && b < c->B) ? c->n[b] : -1;
+}
+int64_t acs_last_launch_count(const acs_ctx* c) { return c ? c->last_launches : -1; }
+
+const char* acs_strerror(acs_status s)
+{
+    switch (s) {
+    case ACS_OK: return "ok";
+    case ACS_EINVAL: return "invalid argument";
+    case ACS_ENOMEM: return "out of memory";
+    case ACS_ECUDA: return "CUDA error or failed device check";
+    case ACS_ETIMEOUT: return "bounded device wait timed out";
+    case ACS_ESTATE: return "context poisoned or no result yet";
+    }
+    return "unknown status";
+}
+
+void acs_destroy(acs_ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// acs_internal.cuh -- types shared by the host side and the kernels of libacs.
+#pragma once
+#include <cstdint>
+
+namespace acs {
+
+constexpr int kMaxCl = 32;          // candidate rows are padded to one warp
+constexpr int kMaxN = 65536;        // edge keys lo*n+hi fit in 32 bits
+constexpr int kMaxM = 1024;         // one ant per thread in the update phase
+constexpr int kCoordLimit = 1 << 20;
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+// Per-instance descriptor (device memory, read-only during a launch).
+struct InstDesc {
+    int32_t n;          // nodes
+    int32_t cl;         // effective candidate width (<= 32, <= n-1)
+    int32_t W;          // 32-bit visited words per ant = ceil(n/32)
+    int32_t instance;   // Philox counter word 3
+    int64_t xy_off;     // coords: xy[2*(xy_off + i) + {0,1}]
+    int64_t row_off;    // candidate rows: nn/w[32*(row_off + c) + k]
+    int64_t tau_off;    // matrix: tau[tau_off + c*n + j]; SPM: slot base spm_*[tau_off + c*s + i]
+    int64_t node_off;   // per-node arrays (SPM tail, best tour): [node_off + c]
+    int64_t tour_off;   // tours[tour_off + a*n + step]
+    int64_t ant_off;    // lens[ant_off + a]
+    int64_t vis_off;    // global visited words (when not in shared memory)
+    float tau0;
+    int32_t pad;
+};
+
+// Kernel arguments of the construct kernel (one iteration of Alg. 1 on every
+// instance of a context).
+struct ConstructArgs {
+    const InstDesc* desc;
+    const int32_t* order;     // instances in longest-first order
+    int32_t num_inst;
+    int32_t m;                // ants
+    const int32_t* xy;
+    const int32_t* nn;        // [rows][32], -1 padded
+    const float* w;           // [rows][32], 0 padded
+    float* tau;               // matrix entries, or SPM trail values
+    int32_t* spm_idx;         // SPM neighbour per slot
+    int32_t* spm_tail;        // SPM tail per node
+    int32_t* tours;
+    int64_t* lens;
+    int32_t* best;            // best-so-far tours [sum n]
+    int64_t* best_len;        // [B], INT64_MAX before the first iteration
+    int64_t* iteration;       // [B]
+    unsigned long long* stats;// [B][4]
+    uint32_t* vis_global;     // visited words when they do not fit in smem
+    const float* P;           // decay table P[0..m]
+    int32_t* status;          // nonzero = an internal check failed
+    float q0, rho;
+    int32_t beta, s, period;
+    uint32_t key0, key1;
+    int32_t vis_in_smem, xy_in_smem, max_n;
+    int32_t H, H2;            // edge / record hash sizes (powers of two)
+};
+
+// Shared-memory carve of the construct kernel; the same arithmetic runs on
+// the host (to size the launch) and on the device (to place the arrays).
+struct SmemLayout {
+    uint32_t P, cur, start, nxt, slot, tsel, len, ekey, ecnt, erep, rkey, rmin,
+        fbant, fbkey, misc, vis, xy, total;
+};
+
+__host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline SmemLayout smem_layout(int m, int H, int H2, int W, int max_n,
+                                                  bool vis_in_smem, bool xy_in_smem)
+{
+    SmemLayout L;
+    uint32_t o = 0;
+    L.P = o;     o = align16(o + 4u * (m + 1));
+    L.cur = o;   o = align16(o + 4u * m);
+    L.start = o; o = align16(o + 4u * m);
+    L.nxt = o;   o = align16(o + 4u * m);
+    L.slot = o;  o = align16(o + 4u * m);
+    L.tsel = o;  o = align16(o + 4u * m);
+    L.len = o;   o = align16(o + 8u * m);
+    L.ekey = o;  o = align16(o + 4u * H);
+    L.ecnt = o;  o = align16(o + 4u * H);
+    L.erep = o;  o = align16(o + 4u * H);
+    L.rkey = o;  o = align16(o + 4u * H2);
+    L.rmin = o;  o = align16(o + 8u * H2);
+    L.fbant = o; o = align16(o + 4u * m);
+    L.fbkey = o; o = align16(o + 8u * m);
+    L.misc = o;  o = align16(o + 512u);
+    L.vis = o;   if (vis_in_smem) o = align16(o + 4u * (uint32_t)m * (uint32_t)W);
+    L.xy = o;    if (xy_in_smem) o = align16(o + 8u * (uint32_t)max_n);
+    L.total = o;
+    return L;
+}
+
+}  // namespace acs

@@ -1,0 +1,156 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer and index results (tours, lengths, SPM slots) and FP32 pheromone
+bytes must be identical: the determinism contract fixes one correct result
+per (instance, parameters, seed).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_02669_gb300 import acs, instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def _pair(xy, memory=0, **kw):
+    p = acs.params(memory=memory, **kw)
+    q = oracle.make_params(memory=memory, **kw)
+    return acs.Colony(xy, p), oracle.Colony(xy, q)
+
+
+def assert_same_state(gpu, ref, memory, b=0):
+    tg, lg = gpu.tours(b)
+    tr, lr = ref.tours()
+    assert np.array_equal(tg, tr), "tours differ (first ant %d)" % int(
+        np.where((tg != tr).any(1))[0][0])
+    assert np.array_equal(lg, lr)
+    bg, blg = gpu.best(b)
+    br, blr = ref.best()
+    assert blg == blr and np.array_equal(bg, br)
+    if memory == 0:
+        a = gpu.pheromone(b).view(np.uint32)
+        r = ref.pheromone().view(np.uint32)
+        assert np.array_equal(a, r), "pheromone differs at %d entries" % int((a != r).sum())
+    else:
+        gv, gi, gt = gpu.pheromone(b)
+        rv, ri, rt = ref.pheromone()
+        assert np.array_equal(gi, ri), "SPM slot indices differ"
+        assert np.array_equal(gt, rt), "SPM tails differ"
+        assert np.array_equal(gv.view(np.uint32), rv.view(np.uint32)), "SPM trails differ"
+    sg = gpu.stats(b)
+    sr = ref.stats()
+    assert sg == sr, (sg, sr)
+
+
+def test_setup_tables_match(oracle_mod):
+    xy = instances.clustered(300, seed=4)
+    gpu, ref = _pair(xy, m=8, cl=32)
+    nn, w, tau0, lnn = gpu.setup()
+    assert np.array_equal(nn, ref.nn)
+    assert np.array_equal(w.view(np.uint32), ref.w.view(np.uint32))
+    assert tau0 == ref.tau0 and lnn == ref.L_nn
+
+
+@pytest.mark.parametrize("memory", [0, 1])
+def test_config_n198_m32_every_iteration(oracle_mod, memory):
+    # n=198 uniform in [0,10000]^2, m=32, 32-NN, beta=2, q0=0.9, rho=xi=0.1, seed 1
+    xy = instances.uniform(198, side=10000, seed=1)
+    gpu, ref = _pair(xy, memory=memory, m=32, cl=32, spm_slots=8, seed=1)
+    for _ in range(8):
+        gpu.run(1)
+        ref.run(1)
+        assert_same_state(gpu, ref, memory)
+
+
+EDGE_CASES = [
+    dict(n=3, m=1, cl=32),
+    dict(n=4, m=3, cl=32, q0=0.0),
+    dict(n=5, m=7, cl=2, q0=1.0),
+    dict(n=9, m=5, cl=8, beta=0),
+    dict(n=31, m=33, cl=32, q0=0.5),
+    dict(n=32, m=16, cl=5, beta=5),
+    dict(n=33, m=40, cl=32, local_period=2),
+    dict(n=65, m=64, cl=16, local_period=3, q0=0.3),
+    dict(n=65, m=9, cl=1, q0=1.0, beta=0),
+    dict(n=100, m=70, cl=10, q0=0.0),
+]
+
+
+@pytest.mark.parametrize("case", EDGE_CASES, ids=lambda c: "-".join("%s%s" % kv for kv in c.items()))
+@pytest.mark.parametrize("memory,slots", [(0, 8), (1, 1), (1, 3), (1, 8)])
+def test_edge_cases(oracle_mod, case, memory, slots):
+    case = dict(case)
+    n = case.pop("n")
+    xy = instances.uniform(n, side=1000, seed=n)
+    gpu, ref = _pair(xy, memory=memory, spm_slots=slots, seed=5, **case)
+    for _ in range(4):
+        gpu.run(1)
+        ref.run(1)
+        assert_same_state(gpu, ref, memory)
+
+
+@pytest.mark.parametrize("memory", [0, 1])
+def test_m128_n1002_clustered(oracle_mod, memory):
+    xy = instances.clustered(1002, seed=2)
+    gpu, ref = _pair(xy, memory=memory, m=128, cl=32, spm_slots=8, seed=1)
+    for _ in range(2):
+        gpu.run(1)
+        ref.run(1)
+    assert_same_state(gpu, ref, memory)
+
+
+@pytest.mark.parametrize("memory", [0, 1])
+def test_full_size_n2392_m128(oracle_mod, memory):
+    # the bench workload's larger instance, one iteration, full state
+    xy = instances.clustered(2392, seed=2)
+    gpu, ref = _pair(xy, memory=memory, m=128, cl=32, spm_slots=8, seed=1)
+    gpu.run(1)
+    ref.run(1)
+    assert_same_state(gpu, ref, memory)
+
+
+def test_visited_in_global_memory_path(oracle_mod):
+    # m=1024 ants on 1200 nodes: the visited bitmasks exceed shared memory
+    xy = instances.uniform(1200, seed=9)
+    gpu, ref = _pair(xy, m=1024, cl=32, q0=0.7, seed=3)
+    gpu.run(1)
+    ref.run(1)
+    assert_same_state(gpu, ref, 0)
+
+
+@pytest.mark.parametrize("memory", [0, 1])
+def test_batch_matches_per_instance_oracle(oracle_mod, memory):
+    sizes = [50, 301, 7, 128, 33, 260]
+    kinds = ["uniform", "clustered"] * 3
+    xy, off = instances.batch(sizes, kinds, seed=4)
+    p = acs.params(m=24, cl=16, memory=memory, spm_slots=6, seed=11)
+    gpu = acs.Colony(xy, p, offsets=off)
+    refs = [oracle.Colony(xy[off[b]:off[b + 1]],
+                          oracle.make_params(m=24, cl=16, memory=memory, spm_slots=6, seed=11),
+                          instance=b) for b in range(len(sizes))]
+    for _ in range(3):
+        gpu.run(1)
+        for r in refs:
+            r.run(1)
+        for b, r in enumerate(refs):
+            assert_same_state(gpu, r, memory, b)
+
+
+def test_repeatable_bits(oracle_mod):
+    xy = instances.clustered(400, seed=6)
+    runs = []
+    for _ in range(3):
+        g = acs.Colony(xy, acs.params(m=64, cl=32, seed=2))
+        g.run(3)
+        runs.append((g.tours()[0], g.pheromone().view(np.uint32)))
+        g.close()
+    for t, tau in runs[1:]:
+        assert np.array_equal(t, runs[0][0]) and np.array_equal(tau, runs[0][1])
