@@ -22,6 +22,8 @@
 // After the closing edges the CTA sums the tour lengths, keeps the best-so-
 // far tour and applies the global update to its n edges.
 #include <cstdint>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "acs_device.cuh"
@@ -635,11 +637,20 @@ static void* select_kernel(int tpa, bool spm)
     }
 }
 
-// Sets the dynamic shared-memory limit (outside any stream capture).
+// Raises the kernel's dynamic shared-memory limit to at least `smem` (outside
+// any stream capture). The limit is a per-function setting shared by every
+// context in the process, so it is only ever raised: lowering it would make
+// the launches of an existing context with a larger layout fail.
 cudaError_t prepare_construct(int tpa, bool spm, size_t smem)
 {
+    static std::mutex mu;
     void* k = select_kernel(tpa, spm);
     if (!k) return cudaErrorInvalidValue;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

@@ -144,6 +144,22 @@ def test_batch_matches_per_instance_oracle(oracle_mod, memory):
             assert_same_state(gpu, r, memory, b)
 
 
+def test_contexts_of_different_sizes_interleaved(oracle_mod):
+    # a large layout created first, a small one second, then both used in turn:
+    # the second context must not break the first one's launches
+    xa = instances.clustered(1002, seed=8)
+    xb = instances.uniform(40, seed=8)
+    ga, ra = _pair(xa, m=128, cl=32, seed=2)
+    gb, rb = _pair(xb, m=4, cl=8, seed=2)
+    for _ in range(2):
+        gb.run(1)
+        rb.run(1)
+        ga.run(1)
+        ra.run(1)
+    assert_same_state(ga, ra, 0)
+    assert_same_state(gb, rb, 0)
+
+
 def test_repeatable_bits(oracle_mod):
     xy = instances.clustered(400, seed=6)
     runs = []
