@@ -317,7 +317,7 @@ def run_ours(args, rank, world, local):
     # end to end through the public API: host coordinates in, best tour out
     # every iteration (pinned host buffers not needed by the C ABI: it copies)
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cols = []
@@ -380,6 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
