@@ -135,6 +135,42 @@ int32_t acs_instance_size(const acs_ctx* ctx, int32_t instance);
 /* Kernel launches made by the last acs_run_iterations call (for accounting). */
 int64_t acs_last_launch_count(const acs_ctx* ctx);
 
+/* No-allocation variant of one iteration (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory, such as code running
+ * inside a memory arena or pool it does not own, or a hot path where
+ * cudaMalloc is not allowed). It runs exactly one iteration of Alg. 1 -- the
+ * same construct kernel and the same results as acs_run_iterations on an
+ * acs_create context -- on one instance whose state lives entirely in
+ * caller-owned DEVICE buffers, FP32 matrix memory only, Philox instance
+ * index 0:
+ *   dev_coords   int32 [n][2] node coordinates (input)
+ *   dev_nn32     int32 [n][32] candidate lists padded with -1 (input)
+ *   dev_w32      float [n][32] heuristic weights padded with 0 (input)
+ *   cl           candidate width used by the rows (1..32, <= n-1)
+ *   tau0         initial trail 1/(n*L_nn)
+ *   dev_tau      float [n][n] pheromone matrix (in/out; start filled with tau0)
+ *   dev_tours    int32 [m][n] tours of this iteration (output)
+ *   dev_lens     int64 [m] their lengths (output)
+ *   dev_best     int32 [n] best-so-far tour (in/out)
+ *   dev_best_len int64 [1] its length (in/out; INT64_MAX before the first call)
+ *   iteration    Philox counter word 0 (0 for the first call, then 1, 2, ...)
+ *   stream       cudaStream_t (NULL = legacy default stream)
+ * The call allocates nothing: its scratch (visited bitmasks, decay table,
+ * descriptor, counters) is one static device array of 4 MiB that every GPU
+ * loading the library keeps until the process exits. Sizes with
+ * m*ceil(n/32) > 1046464 scratch words are rejected with ACS_EINVAL before any
+ * device work. The first call on a device looks the array's address up (once
+ * per device, with that device current); make that first call before any
+ * stream capture. Every call shares the one array: calls that overlap on the
+ * GPU (other streams, other host threads) race and corrupt each other. The
+ * call blocks until the iteration has finished and returns ACS_ECUDA if a
+ * launch or an internal device check failed. */
+acs_status acs_iterate_noalloc(const int32_t* dev_coords, int32_t n, const int32_t* dev_nn32,
+                               const float* dev_w32, int32_t cl, float tau0, float* dev_tau,
+                               int32_t* dev_tours, int64_t* dev_lens, int32_t* dev_best,
+                               int64_t* dev_best_len, int64_t iteration, const acs_params* p,
+                               void* stream);
+
 const char* acs_strerror(acs_status s);
 void acs_destroy(acs_ctx* ctx);
 

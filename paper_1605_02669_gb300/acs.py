@@ -78,7 +78,9 @@ def load():
     L.acs_strerror.restype = ctypes.c_char_p
     L.acs_destroy.argtypes = [_vp]
     L.acs_destroy.restype = None
-    for name in ["acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
+    L.acs_iterate_noalloc.argtypes = [_vp, _i32, _vp, _vp, _i32, ctypes.c_float, _vp, _vp,
+                                      _vp, _vp, _vp, _i64, P(acs_params), _vp]
+    for name in ["acs_iterate_noalloc", "acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
                  "acs_best_tour", "acs_get_tours", "acs_get_pheromone", "acs_get_setup",
                  "acs_get_stats"]:
         getattr(L, name).restype = ctypes.c_int
@@ -190,6 +192,15 @@ def acs_instance_size(ctx, instance):
 
 def acs_last_launch_count(ctx):
     return int(load().acs_last_launch_count(ctx))
+
+
+def acs_iterate_noalloc(dev_coords, n, dev_nn32, dev_w32, cl, tau0, dev_tau, dev_tours,
+                        dev_lens, dev_best, dev_best_len, iteration, p, stream=0):
+    """One iteration on caller-owned device buffers (addresses as ints); no allocation."""
+    return int(load().acs_iterate_noalloc(_vp(dev_coords), int(n), _vp(dev_nn32), _vp(dev_w32),
+                                          int(cl), float(tau0), _vp(dev_tau), _vp(dev_tours),
+                                          _vp(dev_lens), _vp(dev_best), _vp(dev_best_len),
+                                          int(iteration), ctypes.byref(p), _vp(stream or 0)))
 
 
 def acs_destroy(ctx):
