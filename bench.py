@@ -244,11 +244,25 @@ def run_ours(args, rank, world, local):
     sA = torch.cuda.Stream()
     sB = torch.cuda.Stream()
     ctxs = []
-    for mem, st in ((acs.ACS_MEM_MATRIX, sA), (acs.ACS_MEM_SPM, sB)):
+    tuning = {}
+    mems = {"both": (acs.ACS_MEM_MATRIX, acs.ACS_MEM_SPM), "matrix": (acs.ACS_MEM_MATRIX,),
+            "spm": (acs.ACS_MEM_SPM,)}[args.only]
+    for mem, st in zip(mems, (sA, sB)):
         p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
                        seed=1 + rank)
         col = acs.Colony(xy, p, offsets=off)
-        col.set_stream(sA.cuda_stream if st is sA else sB.cuda_stream)
+        col.set_stream(st.cuda_stream)
+        if args.tpa or args.cluster:
+            if args.cluster:
+                col.set_cluster_size(args.cluster)
+            if args.tpa:
+                col.set_threads_per_ant(args.tpa)
+        else:
+            # the autotuner picks lanes per ant and cluster size; the state is
+            # restored afterwards, so the timed iterations are unaffected
+            col.autotune(trial_iters=2)
+        tuning[MEM_NAMES[mem]] = {"threads_per_ant": col.threads_per_ant,
+                                  "cluster_size": col.cluster_size}
         ctxs.append((col, st))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -263,9 +277,10 @@ def run_ours(args, rank, world, local):
         evm0.record(sA)
         ctxs[0][0].run(1)
         evm1.record(sA)
-        ctxs[1][0].run(1)
-        evb.record(sB)
-        sA.wait_event(evb)
+        if len(ctxs) > 1:
+            ctxs[1][0].run(1)
+            evb.record(sB)
+            sA.wait_event(evb)
         ev1.record(sA)
         return ev0, ev1, evm0, evm1
 
@@ -275,6 +290,7 @@ def run_ours(args, rank, world, local):
         step()
     torch.cuda.synchronize()
     fb0 = [ctxs[0][0].stats(b)[0] for b in range(len(SIZES))]
+    units_per_step = sum(M * (n - 1) for n in SIZES) * len(ctxs)
     if world > 1:
         import torch.distributed as dist
 
@@ -290,7 +306,7 @@ def run_ours(args, rank, world, local):
         flush.zero_()
         torch.cuda.synchronize()
         events.append(step())
-        launches += acs.acs_last_launch_count(ctxs[0][0].ctx) + acs.acs_last_launch_count(ctxs[1][0].ctx)
+        launches += sum(acs.acs_last_launch_count(c.ctx) for c, _ in ctxs)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -303,7 +319,7 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     fb1 = [ctxs[0][0].stats(b)[0] for b in range(len(SIZES))]
-    units = ant_steps_per_iter() * args.steps * world
+    units = units_per_step * args.steps * world
     value = units / (total_ms / 1000.0)
 
     # dominant kernel: the matrix construct launch (both matrix instances)
@@ -362,13 +378,17 @@ def run_ours(args, rank, world, local):
         "iterations_per_s": 1000.0 * args.steps / total_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "construct_kernel<8,false> (matrix, n=1002+2392 in one launch)",
+                     "kernel": "construct_kernel<%d,0> (matrix, n=1002+2392 in one launch, "
+                               "clusters of %d)" % (tuning["matrix"]["threads_per_ant"],
+                                                    tuning["matrix"]["cluster_size"])
+                     if "matrix" in tuning else "construct_kernel (SPM only)",
                      "peak_kind": peak_kind,
                      "kernel_ms": float(np.mean(mat_ms))},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(launches),
+        "tuning": tuning,
         "fallback_rate": float(sum(fb_per_launch) / (M * sum(n - 1 for n in SIZES))),
     }
 
@@ -381,6 +401,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--only", choices=["both", "matrix", "spm"], default="both",
+                    help="time only one memory kind (profiling runs; the metric needs both)")
+    ap.add_argument("--tpa", type=int, default=0, help="pin lanes per ant instead of autotuning")
+    ap.add_argument("--cluster", type=int, default=0, help="pin the cluster size instead of autotuning")
     args = ap.parse_args()
     rank, world, local = dist_setup(args)
     if args.impl == "reference":

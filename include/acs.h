@@ -100,6 +100,30 @@ acs_status acs_set_stream(acs_ctx* ctx, void* cuda_stream);
  * asynchronous; replays a captured CUDA graph of one iteration). */
 acs_status acs_run_iterations(acs_ctx* ctx, int32_t iters);
 
+/* Lanes per ant in the construct kernel: 4, 8, 16 or 32. Only
+ * speed depends on it: results are bit-identical for every value. ACS_EINVAL
+ * if the value cannot launch. */
+acs_status acs_set_threads_per_ant(acs_ctx* ctx, int32_t tpa);
+int32_t acs_threads_per_ant(const acs_ctx* ctx);
+
+/* CTAs per thread-block cluster that share one instance: 1, 2, 4, 8 or 16.
+ * Each CTA owns ceil(m/csize) ants; the CTAs exchange each step's edges
+ * through distributed shared memory. The default is the largest size that
+ * leaves at least 16 ants per CTA and keeps every instance resident (with a
+ * full warp per ant when the size is above 1). Only speed depends on it:
+ * results are bit-identical for every value. */
+acs_status acs_set_cluster_size(acs_ctx* ctx, int32_t csize);
+int32_t acs_cluster_size(const acs_ctx* ctx);
+
+/* Autotuner: for every (threads per ant, cluster size) pair that can launch,
+ * times `trial_iters` iterations after one warm-up iteration, restoring the
+ * full colony state after every trial, and keeps the fastest pair (written to
+ * *chosen_tpa / *chosen_csize when not NULL). Results and the iteration count
+ * of the context are unchanged. Synchronous; uses temporary device memory
+ * for the snapshot. */
+acs_status acs_autotune(acs_ctx* ctx, int32_t trial_iters, int32_t* chosen_tpa,
+                        int32_t* chosen_csize);
+
 /* Best-so-far tour (n node indices, 0-based, starting at the ant's first
  * node, closing implicitly) and its length. ACS_ESTATE before the first
  * iteration. */

@@ -80,7 +80,14 @@ def load():
     L.acs_destroy.restype = None
     L.acs_iterate_noalloc.argtypes = [_vp, _i32, _vp, _vp, _i32, ctypes.c_float, _vp, _vp,
                                       _vp, _vp, _vp, _i64, P(acs_params), _vp]
-    for name in ["acs_iterate_noalloc", "acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
+    L.acs_set_threads_per_ant.argtypes = [_vp, _i32]
+    L.acs_threads_per_ant.argtypes = [_vp]
+    L.acs_threads_per_ant.restype = _i32
+    L.acs_autotune.argtypes = [_vp, _i32, _vp, _vp]
+    L.acs_set_cluster_size.argtypes = [_vp, _i32]
+    L.acs_cluster_size.argtypes = [_vp]
+    L.acs_cluster_size.restype = _i32
+    for name in ["acs_set_threads_per_ant", "acs_autotune", "acs_set_cluster_size", "acs_iterate_noalloc", "acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
                  "acs_best_tour", "acs_get_tours", "acs_get_pheromone", "acs_get_setup",
                  "acs_get_stats"]:
         getattr(L, name).restype = ctypes.c_int
@@ -194,6 +201,29 @@ def acs_last_launch_count(ctx):
     return int(load().acs_last_launch_count(ctx))
 
 
+def acs_set_threads_per_ant(ctx, tpa):
+    _check(load().acs_set_threads_per_ant(ctx, int(tpa)), "acs_set_threads_per_ant")
+
+
+def acs_threads_per_ant(ctx):
+    return int(load().acs_threads_per_ant(ctx))
+
+
+def acs_set_cluster_size(ctx, csize):
+    _check(load().acs_set_cluster_size(ctx, int(csize)), "acs_set_cluster_size")
+
+
+def acs_cluster_size(ctx):
+    return int(load().acs_cluster_size(ctx))
+
+
+def acs_autotune(ctx, trial_iters):
+    tpa = np.zeros(1, np.int32)
+    cs = np.zeros(1, np.int32)
+    _check(load().acs_autotune(ctx, int(trial_iters), _ptr(tpa), _ptr(cs)), "acs_autotune")
+    return int(tpa[0]), int(cs[0])
+
+
 def acs_iterate_noalloc(dev_coords, n, dev_nn32, dev_w32, cl, tau0, dev_tau, dev_tours,
                         dev_lens, dev_best, dev_best_len, iteration, p, stream=0):
     """One iteration on caller-owned device buffers (addresses as ints); no allocation."""
@@ -226,6 +256,23 @@ class Colony:
 
     def run(self, iters):
         acs_run_iterations(self.ctx, iters)
+
+    def set_threads_per_ant(self, tpa):
+        acs_set_threads_per_ant(self.ctx, tpa)
+
+    def set_cluster_size(self, csize):
+        acs_set_cluster_size(self.ctx, csize)
+
+    @property
+    def cluster_size(self):
+        return acs_cluster_size(self.ctx)
+
+    @property
+    def threads_per_ant(self):
+        return acs_threads_per_ant(self.ctx)
+
+    def autotune(self, trial_iters=2):
+        return acs_autotune(self.ctx, trial_iters)
 
     def set_stream(self, handle):
         acs_set_stream(self.ctx, handle)

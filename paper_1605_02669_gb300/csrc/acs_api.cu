@@ -17,10 +17,10 @@
 #include "acs_internal.cuh"
 
 namespace acs {
-cudaError_t prepare_construct(int tpa, bool spm, size_t smem);
-cudaError_t launch_construct(const ConstructArgs& A, int tpa, bool spm, int grid, int block,
-                             size_t smem, cudaStream_t stream);
-int construct_occupancy(int tpa, bool spm, int block, size_t smem);
+cudaError_t prepare_construct(int tpa, int mode, size_t smem);
+cudaError_t launch_construct(const ConstructArgs& A, int tpa, int mode, int grid, int block,
+                             size_t smem, int csize, cudaStream_t stream);
+int construct_occupancy(int tpa, int mode, int block, size_t smem, int csize);
 }  // namespace acs
 
 using namespace acs;
@@ -143,6 +143,20 @@ __global__ void init_spm_kernel(const InstDesc* desc, int32_t* idx, float* val, 
         tail[D.node_off + i] = s - 1;
 }
 
+// Heuristic matrix hw[c][j] = eta_cj^beta of every pair (the full scan of the
+// fallback reads it instead of recomputing EUC_2D and the division).
+__global__ void hw_kernel(const InstDesc* desc, const int32_t* xy, float* hw, int beta)
+{
+    const InstDesc D = desc[blockIdx.y];
+    const int2* p = reinterpret_cast<const int2*>(xy) + D.xy_off;
+    const size_t total = (size_t)D.n * D.n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / D.n), j = (int)(i - (size_t)c * D.n);
+        hw[D.hw_off + i] = heuristic(euc2d(p[c], p[j]), beta);
+    }
+}
+
 // ------------------------------------------------------------------ context
 
 struct acs_ctx {
@@ -158,6 +172,7 @@ struct acs_ctx {
     int32_t* d_xy = nullptr;
     int32_t* d_nn = nullptr;
     float* d_w = nullptr;
+    float* d_hw = nullptr;
     float* d_tau = nullptr;
     int32_t* d_spm_idx = nullptr;
     int32_t* d_spm_tail = nullptr;
@@ -178,7 +193,8 @@ struct acs_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     ConstructArgs args{};
-    int tpa = 8, grid = 1, block = 256;
+    int tpa = 8, grid = 1, block = 256, sms = 1, csize = 1, max_smem = 0, mode = 0;
+    bool vis_smem = true, xy_smem = false;
     size_t smem = 0;
     int64_t iteration = 0;
     bool poisoned = false;
@@ -225,13 +241,6 @@ acs_status validate_params(const acs_params* p)
     return ACS_OK;
 }
 
-int next_pow2(int x)
-{
-    int v = 1;
-    while (v < x) v <<= 1;
-    return v;
-}
-
 acs_status fail_cuda(acs_ctx* c, cudaError_t e)
 {
     if (e != cudaSuccess) {
@@ -250,48 +259,104 @@ acs_status fail_cuda(acs_ctx* c, cudaError_t e)
         }                                               \
     } while (0)
 
-cudaError_t plan_launch(acs_ctx* c)
+// Shared-memory plan and block/grid of the construct launch for a
+// (threads-per-ant, cluster size) pair: each CTA of a cluster owns
+// mc = ceil(m/csize) ants, one group of tpa lanes per ant, at least one thread
+// per ant of the instance (the update phase), at most 1024 threads; as many
+// clusters as fit on the GPU, at most one per instance.
+cudaError_t configure(acs_ctx* c, int tpa, int csize)
 {
-    int dev = 0;
-    ACS_TRY(cudaGetDevice(&dev));
-    int max_smem = 0, sms = 0;
-    ACS_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    ACS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int m = c->m;
-    const int H = std::max(64, next_pow2(2 * m));
-    const int H2 = std::max(64, next_pow2(4 * m));
+    const int mc = (m + csize - 1) / csize;
     const int W = (c->max_n + 31) / 32;
-    const SmemLayout base = smem_layout(m, H, H2, W, c->max_n, false, false);
-    bool vis_smem = base.total + 4ull * m * W <= (unsigned long long)max_smem;
-    bool xy_smem = vis_smem && smem_layout(m, H, H2, W, c->max_n, true, true).total <= (uint32_t)max_smem;
-    const SmemLayout L = smem_layout(m, H, H2, W, c->max_n, vis_smem, xy_smem);
-    if (L.total > (uint32_t)max_smem) return cudaErrorInvalidConfiguration;
-    c->smem = L.total;
-    int block = std::min(1024, std::max(64, m * c->tpa));
-    block = (block + 31) / 32 * 32;
-    if (block < m) block = (m + 31) / 32 * 32;
-    c->block = block;
     const bool spm = c->p.memory == ACS_MEM_SPM;
-    ACS_TRY(prepare_construct(c->tpa, spm, c->smem));
-    int occ = construct_occupancy(c->tpa, spm, block, c->smem);
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    c->grid = std::min(c->B, occ * sms);
-    if (!vis_smem) {
+    const uint32_t lim = (uint32_t)c->max_smem;
+    // SPM records resident in shared memory when this CTA's share fits
+    int nrec = 0;
+    if (spm) {
+        const int want = (c->max_n + csize - 1) / csize;
+        if (smem_layout(m, mc, want, c->s, W, c->max_n, false, false).total <= lim) nrec = want;
+    }
+    const int s = c->s;
+    const SmemLayout base = smem_layout(m, mc, nrec, s, W, c->max_n, false, false);
+    const bool vis_smem = base.total + 4ull * mc * W <= (unsigned long long)lim;
+    const bool xy_smem =
+        vis_smem && smem_layout(m, mc, nrec, s, W, c->max_n, true, true).total <= lim;
+    const SmemLayout L = smem_layout(m, mc, nrec, s, W, c->max_n, vis_smem, xy_smem);
+    if (L.total > lim) return cudaErrorInvalidConfiguration;
+    if (!vis_smem && !c->d_vis) {
         size_t words = 0;
         for (int b = 0; b < c->B; ++b) {
             c->desc_h[b].vis_off = (int64_t)words;
             words += (size_t)m * c->desc_h[b].W;
         }
         ACS_TRY(dalloc(c, &c->d_vis, words));
+        ACS_TRY(cudaMemcpy(c->d_desc, c->desc_h.data(), sizeof(InstDesc) * c->B, cudaMemcpyHostToDevice));
     }
+    int block = std::max(mc * tpa, m);
+    block = std::min(1024, std::max(64, block));
+    block = (block + 31) / 32 * 32;
+    if (block < m) return cudaErrorInvalidConfiguration;
+    const int mode = !spm ? 0 : (nrec > 0 ? 2 : 1);
+    ACS_TRY(prepare_construct(tpa, mode, L.total));
+    const int ncl = construct_occupancy(tpa, mode, block, L.total, csize);
+    if (ncl < 1) return cudaErrorInvalidConfiguration;
+    c->tpa = tpa;
+    c->csize = csize;
+    c->mode = mode;
+    c->block = block;
+    c->smem = L.total;
+    c->vis_smem = vis_smem;
+    c->xy_smem = xy_smem;
+    c->grid = std::min(c->B, ncl) * csize;
+    c->args.vis_in_smem = vis_smem ? 1 : 0;
+    c->args.xy_in_smem = xy_smem ? 1 : 0;
+    c->args.vis_global = c->d_vis;
+    c->args.mc = mc;
+    c->args.nrec = nrec;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    return cudaSuccess;
+}
+
+// Default cluster size: the largest power of two up to 16 that leaves at
+// least 16 ants per CTA and lets every instance's cluster be resident at once.
+int default_cluster_size(const acs_ctx* c)
+{
+    int cs = 16;
+    while (cs > 1 && (c->m / cs < 16 || c->B * cs > c->sms)) cs >>= 1;
+    return cs;
+}
+
+// Default lanes per ant: a full warp per ant when an instance spans a cluster
+// (few instances, latency-bound steps); 8 lanes otherwise, so that several
+// CTAs share an SM when many instances run at once.
+int default_tpa(const acs_ctx* c, int cs)
+{
+    if (cs == 1) return 8;
+    const int mc = (c->m + cs - 1) / cs;
+    int tpa = 32;
+    while (tpa > 4 && mc * tpa > 1024) tpa >>= 1;
+    return tpa;
+}
+
+cudaError_t plan_launch(acs_ctx* c)
+{
+    int dev = 0;
+    ACS_TRY(cudaGetDevice(&dev));
+    ACS_TRY(cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    ACS_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
     ConstructArgs& A = c->args;
     A.desc = c->d_desc;
     A.order = c->d_order;
     A.num_inst = c->B;
-    A.m = m;
+    A.m = c->m;
     A.xy = c->d_xy;
     A.nn = c->d_nn;
     A.w = c->d_w;
+    A.hw = c->d_hw;
     A.tau = c->d_tau;
     A.spm_idx = c->d_spm_idx;
     A.spm_tail = c->d_spm_tail;
@@ -301,7 +366,6 @@ cudaError_t plan_launch(acs_ctx* c)
     A.best_len = c->d_best_len;
     A.iteration = c->d_iter;
     A.stats = c->d_stats;
-    A.vis_global = c->d_vis;
     A.P = c->d_P;
     A.status = c->d_status;
     A.q0 = c->p.q0;
@@ -311,12 +375,15 @@ cudaError_t plan_launch(acs_ctx* c)
     A.period = c->p.local_period;
     A.key0 = (uint32_t)(c->p.seed & 0xffffffffull);
     A.key1 = (uint32_t)(c->p.seed >> 32);
-    A.vis_in_smem = vis_smem ? 1 : 0;
-    A.xy_in_smem = xy_smem ? 1 : 0;
     A.max_n = c->max_n;
-    A.H = H;
-    A.H2 = H2;
-    return cudaSuccess;
+    // largest cluster that fits, falling back to smaller ones
+    for (int cs = default_cluster_size(c); cs >= 1; cs >>= 1) {
+        cudaError_t e = configure(c, default_tpa(c, cs), cs);
+        if (e == cudaSuccess) return e;
+        if (e != cudaErrorInvalidConfiguration) return e;
+        cudaGetLastError();
+    }
+    return cudaErrorInvalidConfiguration;
 }
 
 cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
@@ -339,6 +406,7 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
         D.tour_off = (int64_t)tour_total;
         D.ant_off = (int64_t)b * m;
         D.vis_off = 0;
+        D.hw_off = D.tau_off;
         D.tau0 = 0.0f;
         D.pad = 0;
         tau_total += c->p.memory == ACS_MEM_MATRIX ? (size_t)n * n : (size_t)n * c->s;
@@ -356,6 +424,21 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     ACS_TRY(dalloc(c, &c->d_xy, 2 * (size_t)total_n));
     ACS_TRY(dalloc(c, &c->d_nn, 32 * (size_t)total_n));
     ACS_TRY(dalloc(c, &c->d_w, 32 * (size_t)total_n));
+    // heuristic matrix for the full scan, when all instances' n^2 floats fit
+    // the budget (always for the matrix memory, whose offsets it shares)
+    size_t hw_total = 0;
+    for (int b = 0; b < B; ++b) hw_total += (size_t)c->n[b] * c->n[b];
+    const size_t kHwBudget = (size_t)64 << 30;
+    if (hw_total * sizeof(float) <= kHwBudget) {
+        if (c->p.memory == ACS_MEM_SPM) {
+            size_t off = 0;
+            for (int b = 0; b < B; ++b) {
+                c->desc_h[b].hw_off = (int64_t)off;
+                off += (size_t)c->n[b] * c->n[b];
+            }
+        }
+        ACS_TRY(dalloc(c, &c->d_hw, hw_total));
+    }
     ACS_TRY(dalloc(c, &c->d_tau, tau_total));
     if (c->p.memory == ACS_MEM_SPM) {
         ACS_TRY(dalloc(c, &c->d_spm_idx, tau_total));
@@ -395,6 +478,10 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     nn_tour_kernel<<<B, 1024, vis_bytes, st>>>(c->d_desc, c->d_xy, c->d_Lnn);
     ACS_TRY(cudaGetLastError());
     dim3 ig(256, B);
+    if (c->d_hw) {
+        hw_kernel<<<dim3(1024, B), 256, 0, st>>>(c->d_desc, c->d_xy, c->d_hw, c->p.beta);
+        ACS_TRY(cudaGetLastError());
+    }
     if (c->p.memory == ACS_MEM_MATRIX) {
         init_matrix_kernel<<<ig, 256, 0, st>>>(c->d_desc, c->d_tau);
     } else {
@@ -505,11 +592,11 @@ acs_status acs_run_iterations(acs_ctx* c, int32_t iters)
     if (c->poisoned) return ACS_ESTATE;
     c->last_launches = 0;
     if (iters == 0) return ACS_OK;
-    const bool spm = c->p.memory == ACS_MEM_SPM;
     if (!c->exec) {
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return fail_cuda(c, e);
-        cudaError_t le = launch_construct(c->args, c->tpa, spm, c->grid, c->block, c->smem, c->stream);
+        cudaError_t le = launch_construct(c->args, c->tpa, c->mode, c->grid, c->block, c->smem,
+                                          c->csize, c->stream);
         e = cudaStreamEndCapture(c->stream, &c->graph);
         if (le != cudaSuccess) return fail_cuda(c, le);
         if (e != cudaSuccess) return fail_cuda(c, e);
@@ -522,6 +609,112 @@ acs_status acs_run_iterations(acs_ctx* c, int32_t iters)
     }
     c->iteration += iters;
     c->last_launches = iters;
+    return ACS_OK;
+}
+
+acs_status acs_set_threads_per_ant(acs_ctx* c, int32_t tpa)
+{
+    if (!c || (tpa != 4 && tpa != 8 && tpa != 16 && tpa != 32)) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    cudaError_t e = configure(c, tpa, c->csize);
+    if (e == cudaErrorInvalidConfiguration) {
+        cudaGetLastError();
+        return ACS_EINVAL;
+    }
+    return fail_cuda(c, e);
+}
+
+int32_t acs_threads_per_ant(const acs_ctx* c) { return c ? c->tpa : -1; }
+
+acs_status acs_set_cluster_size(acs_ctx* c, int32_t csize)
+{
+    if (!c || (csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16)) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    cudaError_t e = configure(c, c->tpa, csize);
+    if (e == cudaErrorInvalidConfiguration) {
+        cudaGetLastError();
+        return ACS_EINVAL;
+    }
+    return fail_cuda(c, e);
+}
+
+int32_t acs_cluster_size(const acs_ctx* c) { return c ? c->csize : -1; }
+
+acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
+                        int32_t* chosen_csize)
+{
+    if (!c || trial_iters < 1) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    // every mutable array of the context, restored after each trial
+    struct Buf { void* p; size_t bytes; void* save; };
+    size_t tau_n = 0, tour_n = 0, node_n = 0;
+    for (int b = 0; b < c->B; ++b) {
+        const size_t n = (size_t)c->n[b];
+        tau_n += c->p.memory == ACS_MEM_MATRIX ? n * n : n * c->s;
+        tour_n += (size_t)c->m * n;
+        node_n += n;
+    }
+    std::vector<Buf> bufs = {
+        {c->d_tau, sizeof(float) * tau_n, nullptr},
+        {c->d_tours, sizeof(int32_t) * tour_n, nullptr},
+        {c->d_lens, sizeof(int64_t) * (size_t)c->B * c->m, nullptr},
+        {c->d_best, sizeof(int32_t) * node_n, nullptr},
+        {c->d_best_len, sizeof(int64_t) * c->B, nullptr},
+        {c->d_iter, sizeof(int64_t) * c->B, nullptr},
+        {c->d_stats, sizeof(unsigned long long) * 4 * c->B, nullptr},
+    };
+    if (c->p.memory == ACS_MEM_SPM) {
+        bufs.push_back({c->d_spm_idx, sizeof(int32_t) * tau_n, nullptr});
+        bufs.push_back({c->d_spm_tail, sizeof(int32_t) * node_n, nullptr});
+    }
+    acs_status st = ACS_OK;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    for (Buf& x : bufs) {
+        if (cudaMalloc(&x.save, x.bytes) != cudaSuccess) { cudaGetLastError(); st = ACS_ENOMEM; break; }
+        if (cudaMemcpy(x.save, x.p, x.bytes, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+            st = fail_cuda(c, cudaErrorUnknown);
+            break;
+        }
+    }
+    const int64_t iter0 = c->iteration;
+    int best_tpa = c->tpa, best_cs = c->csize;
+    float best_ms = 0.0f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == ACS_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail_cuda(c, cudaErrorUnknown);
+    const int tpas[4] = {4, 8, 16, 32};
+    const int css[5] = {1, 2, 4, 8, 16};
+    for (int ci = 0; ci < 5 && st == ACS_OK; ++ci) {
+        for (int ti = 0; ti < 4 && st == ACS_OK; ++ti) {
+            if (css[ci] > c->m) continue;
+            if (configure(c, tpas[ti], css[ci]) != cudaSuccess) { cudaGetLastError(); continue; }
+            st = acs_run_iterations(c, 1);  // warm-up, captures the graph
+            if (st != ACS_OK) break;
+            cudaEventRecord(e0, c->stream);
+            st = acs_run_iterations(c, trial_iters);
+            if (st != ACS_OK) break;
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail_cuda(c, cudaErrorUnknown); break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best_tpa = tpas[ti]; best_cs = css[ci]; }
+            for (Buf& x : bufs)
+                if (cudaMemcpy(x.p, x.save, x.bytes, cudaMemcpyDeviceToDevice) != cudaSuccess)
+                    st = fail_cuda(c, cudaErrorUnknown);
+            c->iteration = iter0;
+        }
+    }
+    for (Buf& x : bufs) if (x.save) cudaFree(x.save);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->iteration = iter0;
+    c->last_launches = 0;
+    if (st != ACS_OK) return st;
+    if (configure(c, best_tpa, best_cs) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    if (chosen_tpa) *chosen_tpa = best_tpa;
+    if (chosen_csize) *chosen_csize = best_cs;
     return ACS_OK;
 }
 

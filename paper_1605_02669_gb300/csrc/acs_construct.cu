@@ -1,47 +1,64 @@
 // acs_construct.cu -- the construct kernel: one full iteration of the Ant
-// Colony System (Alg. 1) per instance, one CTA per instance.
+// Colony System (Alg. 1) per instance, one thread-block cluster per instance.
 //
-// Mapping. A group of TPA consecutive lanes builds one ant's tour; lane l of
-// the group owns candidate ranks l*V .. l*V+V-1 (V = 32/TPA), so the
-// 128-byte candidate row (node index and heuristic weight, padded to 32) is
-// read with one vector load per lane. Groups loop over ants when m exceeds
-// the groups of the CTA. Per step:
-//   A  every ant reads its candidate row, the visited bitmask (shared memory
-//      when it fits), the pheromone of the unvisited candidates (a gather
-//      from row c of the matrix, or a probe of record c of the SPM), draws
-//      Philox(iteration, ant, step, instance) and applies Eq. 1-2 with a
-//      group argmax (q < q0) or a Hillis-Steele roulette (Sec. 3.1.1). An ant
-//      whose candidate set is empty is queued.
-//   B  the whole CTA scans all nodes for each queued ant and reduces the
-//      argmax of tau*eta^beta with 64-bit shared atomics (the block-level
-//      full scan of Sec. 3.1.1, here shared by all queued ants).
-//   C  the step's edges, deduplicated in a shared hash table, receive one
-//      folded local update each (Eq. 3 applied k times in closed form):
-//      matrix entries are written in both halves; SPM records are updated in
-//      rounds so that each record sees its events in (ant, side) order.
-// After the closing edges the CTA sums the tour lengths, keeps the best-so-
-// far tour and applies the global update to its n edges.
+// Mapping. The C CTAs of a cluster share one instance; CTA r owns ants
+// r*mc .. r*mc+mc-1 (their visited bitmasks live in its shared memory). A
+// group of TPA consecutive lanes builds one ant's tour; lane l of the group
+// owns candidate ranks l*V .. l*V+V-1 (V = 32/TPA), so the 128-byte
+// candidate row (node index and heuristic weight, padded to 32) is read with
+// vector loads. Per construction step:
+//   A  every ant reads its candidate row, its visited bits, the pheromone of
+//      the unvisited candidates (a gather from row c of the matrix, or a probe
+//      of record c of the SPM), draws Philox(iteration, ant, step, instance)
+//      and applies Eq. 1-2: a group argmax of tau*eta^beta (q < q0) or a
+//      Hillis-Steele roulette (Sec. 3.1.1). An ant whose candidate set is
+//      empty is queued.
+//   B  ants whose candidate set is empty are queued with the step's edges.
+//      After the first cluster barrier every CTA scans its 1/C slice of the
+//      nodes for every queued ant of the cluster (the ant's visited bits are
+//      read through distributed shared memory) and merges its partial argmax
+//      of tau*eta^beta (ties -> lowest node) in its own shared memory; after a
+//      second barrier the owner (and every CTA that needs the edge) takes the
+//      maximum of the C partial results: the block-level reduction of
+//      Sec. 3.1.1 spread over the cluster.
+//   C  every CTA reads all m edges through distributed shared memory and
+//      counts equal undirected edges (no atomics: each edge is compared with
+//      all others by a few threads). An edge taken by k ants gets
+//      one folded local update (Eq. 3 applied k times in closed form): on the
+//      matrix the CTA of the lowest such ant writes both halves; on the SPM
+//      record r is updated by CTA r mod C, which replays that record's events
+//      in (ant, side) order (Alg. 3). A second cluster barrier publishes the
+//      writes before the next step.
+// After the closing edges the cluster sums the tour lengths, keeps the
+// best-so-far tour and applies the global update to its n edges.
+//
+// Mutable global state (pheromone, SPM records, best tour) is written by one
+// SM and read by others after a cluster barrier, so it is always read with
+// L2-coherent loads (ld.global.cg).
 #include <cstdint>
 #include <mutex>
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "acs_device.cuh"
 #include "acs_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace acs {
 
 namespace {
 
 struct Misc {
-    int fbcount;
+    int qn[2];                    // queued ants of this CTA, by step parity
     int improved;
     int bestant;
-    int pad;
     unsigned long long stat[4];   // fallback, selections, spm hits, spm misses
-    unsigned long long red[32];
     long long best_len;
     long long iteration;
+    int qoff[20];                 // prefix sums of the cluster's queues
+    int nrel;                     // edges this CTA writes in the current step
 };
 
 __device__ __forceinline__ bool visited(const uint32_t* vis, int j)
@@ -49,71 +66,51 @@ __device__ __forceinline__ bool visited(const uint32_t* vis, int j)
     return (vis[j >> 5] >> (j & 31)) & 1u;
 }
 
-__device__ __forceinline__ int2 load_xy(const int2* xy, int j)
+// Loads of mutable state: records in shared memory (local or another CTA's,
+// through a generic pointer) are read directly; global state is read at L2
+// (ld.global.cg) because other SMs of the cluster may have written it.
+template <bool GLOBAL>
+__device__ __forceinline__ int ld_i(const int32_t* p)
 {
-    return xy[j];
+    if constexpr (GLOBAL) return __ldcg(p);
+    else return *p;
 }
 
-// Probe record c of the SPM for neighbour j (absent -> tau0).
-__device__ __forceinline__ float spm_read(const int32_t* idx, const float* val, int s, int j,
-                                          float tau0)
+template <bool GLOBAL>
+__device__ __forceinline__ float ld_f(const float* p)
 {
-    float t = tau0;
-    for (int i = 0; i < s; ++i)
-        if (idx[i] == j) t = val[i];
-    return t;
+    if constexpr (GLOBAL) return __ldcg(p);
+    else return *p;
 }
+
+// One SPM record (Sec. 3.2): s neighbour indices, s trails, the tail.
+struct Rec {
+    int32_t* idx;
+    float* val;
+    int32_t* tail;
+};
 
 // Alg. 3 on one record: a hit updates in place, a miss evicts the slot after
 // tail. mode 0 = local (coef = P[k]), 1 = global (coef = rho, target = Delta).
-__device__ __forceinline__ bool spm_apply(int32_t* idx, float* val, int32_t* tail, int s,
-                                          int nb, float tau0, int mode, float coef, float target)
+template <bool GLOBAL>
+__device__ __forceinline__ bool spm_apply(const Rec& R, int s, int nb, float tau0, int mode,
+                                          float coef, float target)
 {
-    for (int i = 0; i < s; ++i) {
-        if (idx[i] == nb) {
-            const float t = val[i];
-            val[i] = mode == 0 ? local_rule(t, tau0, coef) : global_rule(t, target, coef);
-            return true;
-        }
+    int hit = -1;
+#pragma unroll 8
+    for (int i = 0; i < s; ++i)
+        if (ld_i<GLOBAL>(R.idx + i) == nb) hit = i;
+    if (hit >= 0) {
+        const float t = ld_f<GLOBAL>(R.val + hit);
+        R.val[hit] = mode == 0 ? local_rule(t, tau0, coef) : global_rule(t, target, coef);
+        return true;
     }
-    int t = *tail + 1;
+    int t = ld_i<GLOBAL>(R.tail) + 1;
     if (t == s) t = 0;
-    *tail = t;
-    idx[t] = nb;
-    val[t] = mode == 0 ? local_rule(tau0, tau0, coef) : global_rule(tau0, target, coef);
+    *R.tail = t;
+    R.idx[t] = nb;
+    R.val[t] = mode == 0 ? local_rule(tau0, tau0, coef) : global_rule(tau0, target, coef);
     return false;
-}
-
-// Edge hash insert: returns the slot; counts visits and keeps the lowest ant.
-__device__ __forceinline__ int edge_insert(uint32_t* ekey, int* ecnt, int* erep, int H,
-                                           uint32_t key, int ant, int32_t* status)
-{
-    const int shift = 32 - __ffs(H) + 1;
-    int slot = (int)(hash32(key) >> shift);
-    for (int probe = 0; probe < H; ++probe) {
-        const uint32_t old = atomicCAS(&ekey[slot], kEmpty, key);
-        if (old == kEmpty || old == key) {
-            atomicAdd(&ecnt[slot], 1);
-            atomicMin(&erep[slot], ant);
-            return slot;
-        }
-        slot = (slot + 1) & (H - 1);
-    }
-    atomicExch(status, 2);
-    return 0;
-}
-
-__device__ __forceinline__ int rec_insert(uint32_t* rkey, int H2, uint32_t rec, int32_t* status)
-{
-    const int shift = 32 - __ffs(H2) + 1;
-    int slot = (int)(hash32(rec) >> shift);
-    for (int probe = 0; probe < H2; ++probe) {
-        const uint32_t old = atomicCAS(&rkey[slot], kEmpty, rec);
-        if (old == kEmpty || old == rec) return slot;
-        slot = (slot + 1) & (H2 - 1);
-    }
-    atomicExch(status, 3);
-    return 0;
 }
 
 template <int TPA>
@@ -123,13 +120,95 @@ __device__ __forceinline__ unsigned group_mask(int lane)
     else return ((1u << TPA) - 1u) << (lane & ~(TPA - 1));
 }
 
+// (product bits, node) packed so that the larger product wins and, among
+// equal products, the lower node index.
+__device__ __forceinline__ unsigned long long pack_pj(float p, int j)
+{
+    return ((unsigned long long)__float_as_uint(p) << 32) |
+           (unsigned long long)(0xffffffffu - (uint32_t)j);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, k, off);
+        k = o > k ? o : k;
+    }
+    return k;
+}
+
+template <int V>
+__device__ __forceinline__ void load_row(const int32_t* nrow, const float* wrow, int* nv, float* wv)
+{
+    if constexpr (V == 8) {
+        const int4 t0 = reinterpret_cast<const int4*>(nrow)[0];
+        const int4 t1 = reinterpret_cast<const int4*>(nrow)[1];
+        const float4 u0 = reinterpret_cast<const float4*>(wrow)[0];
+        const float4 u1 = reinterpret_cast<const float4*>(wrow)[1];
+        nv[0] = t0.x; nv[1] = t0.y; nv[2] = t0.z; nv[3] = t0.w;
+        nv[4] = t1.x; nv[5] = t1.y; nv[6] = t1.z; nv[7] = t1.w;
+        wv[0] = u0.x; wv[1] = u0.y; wv[2] = u0.z; wv[3] = u0.w;
+        wv[4] = u1.x; wv[5] = u1.y; wv[6] = u1.z; wv[7] = u1.w;
+    } else if constexpr (V == 4) {
+        const int4 t = *reinterpret_cast<const int4*>(nrow);
+        const float4 u = *reinterpret_cast<const float4*>(wrow);
+        nv[0] = t.x; nv[1] = t.y; nv[2] = t.z; nv[3] = t.w;
+        wv[0] = u.x; wv[1] = u.y; wv[2] = u.z; wv[3] = u.w;
+    } else if constexpr (V == 2) {
+        const int2 t = *reinterpret_cast<const int2*>(nrow);
+        const float2 u = *reinterpret_cast<const float2*>(wrow);
+        nv[0] = t.x; nv[1] = t.y;
+        wv[0] = u.x; wv[1] = u.y;
+    } else {
+        nv[0] = nrow[0];
+        wv[0] = wrow[0];
+    }
+}
+
 }  // namespace
 
-template <int TPA, bool SPM>
+// Total of `v` over the T consecutive lanes of this lane's segment.
+template <typename Tv>
+__device__ __forceinline__ Tv seg_sum(Tv v, int T)
+{
+    for (int off = T / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, T);
+    return v;
+}
+
+__device__ __forceinline__ int seg_min(int v, int T)
+{
+    for (int off = T / 2; off >= 1; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off, T));
+    return v;
+}
+
+// Maximum of entry `ent` over the C CTAs' partial results (C <= 16): the
+// loads are independent, so they are all issued before the first use.
+__device__ __forceinline__ unsigned long long cluster_max_entry(cg::cluster_group& cluster,
+                                                                unsigned long long* part, int ent,
+                                                                int C)
+{
+    unsigned long long k[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) k[r] = r < C ? cluster.map_shared_rank(part, r)[ent] : 0ull;
+    unsigned long long key = 0ull;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) key = k[r] > key ? k[r] : key;
+    return key;
+}
+
+// MODE 0: pheromone matrix. MODE 1: SPM records in global memory. MODE 2: SPM
+// record r resident, for the launch, in the shared memory of CTA r mod C
+// (loaded at the start, written back after the global update); other CTAs
+// read it through distributed shared memory.
+template <int TPA, int MODE>
 __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs A)
 {
+    constexpr bool SPM = MODE != 0;
+    constexpr bool RG = MODE == 1;   // SPM record loads go through L2
     constexpr int V = 32 / TPA;
     extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31;
@@ -137,103 +216,141 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
     const int group = tid / TPA;
     const int ngroups = nthr / TPA;
     const unsigned gmask = group_mask<TPA>(lane);
+    const int gbase = lane & ~(TPA - 1);
     const int m = A.m;
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int mc = A.mc;
+    const int a0 = rank * mc;
+    const int ml = max(0, min(m, a0 + mc) - a0);   // ants owned by this CTA
+    const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+    const int s_slots = A.s;
 
-    for (int oi = blockIdx.x; oi < A.num_inst; oi += gridDim.x) {
+    for (int oi = cid; oi < A.num_inst; oi += ncl) {
         const int b = A.order[oi];
         const InstDesc D = A.desc[b];
         const int n = D.n, cl = D.cl, W = D.W;
         const float tau0 = D.tau0;
-        const SmemLayout L = smem_layout(m, A.H, A.H2, W, A.max_n, A.vis_in_smem, A.xy_in_smem);
+        const SmemLayout L = smem_layout(m, mc, A.nrec, s_slots, W, A.max_n, A.vis_in_smem,
+                                         A.xy_in_smem);
         float* sP = (float*)(smem + L.P);
         int* s_cur = (int*)(smem + L.cur);
         int* s_start = (int*)(smem + L.start);
         int* s_nxt = (int*)(smem + L.nxt);
-        int* s_slot = (int*)(smem + L.slot);
         float* s_tsel = (float*)(smem + L.tsel);
         long long* s_len = (long long*)(smem + L.len);
-        uint32_t* ekey = (uint32_t*)(smem + L.ekey);
-        int* ecnt = (int*)(smem + L.ecnt);
-        int* erep = (int*)(smem + L.erep);
-        uint32_t* rkey = (uint32_t*)(smem + L.rkey);
-        uint32_t* rmin = (uint32_t*)(smem + L.rmin);  // two buffers of H2
-        int* fbant = (int*)(smem + L.fbant);
-        unsigned long long* fbkey = (unsigned long long*)(smem + L.fbkey);
+        uint32_t* pedge = (uint32_t*)(smem + L.pedge);   // (u << 16) | v, or queued | index
+        int* qant = (int*)(smem + L.qant);
+        int* qc = (int*)(smem + L.qc);
+        unsigned long long* qpart = (unsigned long long*)(smem + L.qpart);  // by cluster entry
+        int* eqc = (int*)(smem + L.eqc);
+        int* eqown = (int*)(smem + L.eqown);
+        int* eqal = (int*)(smem + L.eqal);
+        uint32_t* gkey = (uint32_t*)(smem + L.gkey);
+        int* gu = (int*)(smem + L.gu);
+        int* gv = (int*)(smem + L.gv);
+        int* grep = (int*)(smem + L.grep);
+        int* gcnt = (int*)(smem + L.gcnt);
+        int* ev0 = (int*)(smem + L.ev0);
+        int* ev1 = (int*)(smem + L.ev1);
+        int* fri = (int*)(smem + L.fri);
+        float* frv = (float*)(smem + L.frv);
         Misc* misc = (Misc*)(smem + L.misc);
-        uint32_t* vis_base = A.vis_in_smem ? (uint32_t*)(smem + L.vis) : A.vis_global + D.vis_off;
+        int32_t* ridx_s = (int32_t*)(smem + L.ridx);
+        float* rval_s = (float*)(smem + L.rval);
+        int32_t* rtail_s = (int32_t*)(smem + L.rtail);
+        uint32_t* vis_base = A.vis_in_smem ? (uint32_t*)(smem + L.vis)
+                                           : A.vis_global + D.vis_off + (size_t)a0 * W;
         const int2* xy = A.xy_in_smem ? (const int2*)(smem + L.xy)
                                       : (const int2*)(A.xy) + D.xy_off;
         const int32_t* nn_rows = A.nn + 32 * D.row_off;
         const float* w_rows = A.w + 32 * D.row_off;
+        const float* hw = A.hw ? A.hw + D.hw_off : nullptr;
         float* tau = A.tau + D.tau_off;           // matrix rows, or SPM values
         int32_t* sidx = A.spm_idx + D.tau_off;    // SPM only
         int32_t* stail = A.spm_tail + D.node_off; // SPM only
         int32_t* tours = A.tours + D.tour_off;
         int32_t* best = A.best + D.node_off;
-        const int s_slots = A.s;
+
+        // SPM record r: this CTA's shared copy, another CTA's through DSMEM, or global
+        auto rec = [&](int r) -> Rec {
+            if constexpr (MODE == 2) {
+                const int o = r % C, li = r / C;
+                if (o == rank) return Rec{ridx_s + li * s_slots, rval_s + li * s_slots, rtail_s + li};
+                return Rec{cluster.map_shared_rank(ridx_s, o) + li * s_slots,
+                           cluster.map_shared_rank(rval_s, o) + li * s_slots,
+                           cluster.map_shared_rank(rtail_s, o) + li};
+            } else {
+                return Rec{sidx + (size_t)r * s_slots, tau + (size_t)r * s_slots, stail + r};
+            }
+        };
+        // visited bitmask of ant al of CTA r (for the cluster-wide full scan)
+        auto vis_of = [&](int r, int al) -> const uint32_t* {
+            if (A.vis_in_smem) return cluster.map_shared_rank(vis_base, r) + (size_t)al * W;
+            return A.vis_global + D.vis_off + (size_t)(r * mc + al) * W;
+        };
 
         // ---- per-instance shared set-up
         for (int i = tid; i <= m; i += nthr) sP[i] = A.P[i];
-        for (int i = tid; i < A.H; i += nthr) { ekey[i] = kEmpty; ecnt[i] = 0; erep[i] = 0x7fffffff; }
-        for (int i = tid; i < A.H2; i += nthr) { rkey[i] = kEmpty; rmin[i] = kEmpty; rmin[A.H2 + i] = kEmpty; }
         if (A.xy_in_smem) {
             const int2* gxy = (const int2*)(A.xy) + D.xy_off;
             int2* sxy = (int2*)(smem + L.xy);
             for (int i = tid; i < n; i += nthr) sxy[i] = gxy[i];
         }
+        if constexpr (MODE == 2) {
+            for (int li = tid; li < A.nrec; li += nthr) {
+                const int r = rank + li * C;
+                if (r >= n) continue;
+                for (int q = 0; q < s_slots; ++q) {
+                    ridx_s[li * s_slots + q] = __ldcg(sidx + (size_t)r * s_slots + q);
+                    rval_s[li * s_slots + q] = __ldcg(tau + (size_t)r * s_slots + q);
+                }
+                rtail_s[li] = __ldcg(stail + r);
+            }
+        }
         if (tid == 0) {
-            misc->fbcount = 0;
-            misc->best_len = A.best_len[b];
-            misc->iteration = A.iteration[b];
+            misc->qn[0] = 0;
+            misc->qn[1] = 0;
+            misc->best_len = __ldcg(A.best_len + b);
+            misc->iteration = __ldcg(A.iteration + b);
             for (int i = 0; i < 4; ++i) misc->stat[i] = 0ull;
         }
-        for (int i = tid; i < m * W; i += nthr) vis_base[i] = 0u;
+        for (int i = tid; i < ml * W; i += nthr) vis_base[i] = 0u;
         __syncthreads();
 
         const uint32_t it = (uint32_t)misc->iteration;
         const uint32_t inst = (uint32_t)D.instance;
 
         // ---- step 0: first node of every ant (Alg. 1, uniform draw)
-        for (int a = tid; a < m; a += nthr) {
+        for (int al = tid; al < ml; al += nthr) {
+            const int a = a0 + al;
             const uint4 x = philox4x32_10(make_uint4(it, (uint32_t)a, 0u, inst), A.key0, A.key1);
             const int start = (int)__umulhi(x.z, (uint32_t)n);
-            s_cur[a] = start;
-            s_start[a] = start;
+            s_cur[al] = start;
+            s_start[al] = start;
             tours[(size_t)a * n] = start;
-            vis_base[(size_t)a * W + (start >> 5)] |= 1u << (start & 31);
+            vis_base[(size_t)al * W + (start >> 5)] |= 1u << (start & 31);
         }
-        __syncthreads();
+        cluster.sync();
 
-        unsigned long long n_fb = 0, n_sel = 0, n_hit = 0, n_miss = 0;
+        unsigned long long n_fb = 0, n_hit = 0, n_miss = 0;
 
         // ---- steps 1 .. n (n = the closing edges)
         for (int step = 1; step <= n; ++step) {
             const bool closing = (step == n);
             const bool upd = (step % A.period) == 0;
+            int* qn = &misc->qn[step & 1];
 
             if (!closing) {
                 // Phase A: pseudo-random-proportional rule on the candidate list
-                for (int a = group; a < m; a += ngroups) {
-                    const int c = s_cur[a];
-                    const uint32_t* vis = vis_base + (size_t)a * W;
-                    const int32_t* nrow = nn_rows + (size_t)c * 32 + gl * V;
-                    const float* wrow = w_rows + (size_t)c * 32 + gl * V;
+                for (int al = group; al < ml; al += ngroups) {
+                    const int a = a0 + al;
+                    const int c = s_cur[al];
+                    const uint32_t* vis = vis_base + (size_t)al * W;
                     int nv[V];
                     float wv[V];
-                    if (V == 4) {
-                        const int4 t = *reinterpret_cast<const int4*>(nrow);
-                        const float4 u = *reinterpret_cast<const float4*>(wrow);
-                        nv[0] = t.x; nv[1] = t.y; nv[2 % V] = t.z; nv[3 % V] = t.w;
-                        wv[0] = u.x; wv[1] = u.y; wv[2 % V] = u.z; wv[3 % V] = u.w;
-                    } else if (V == 2) {
-                        const int2 t = *reinterpret_cast<const int2*>(nrow);
-                        const float2 u = *reinterpret_cast<const float2*>(wrow);
-                        nv[0] = t.x; nv[1 % V] = t.y;
-                        wv[0] = u.x; wv[1 % V] = u.y;
-                    } else {
-                        nv[0] = nrow[0];
-                        wv[0] = wrow[0];
-                    }
+                    load_row<V>(nn_rows + (size_t)c * 32 + gl * V, w_rows + (size_t)c * 32 + gl * V,
+                                nv, wv);
                     bool unv[V];
                     bool lane_any = false;
 #pragma unroll
@@ -245,25 +362,26 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     const unsigned anyb = __ballot_sync(gmask, lane_any) & gmask;
                     if (anyb == 0u) {
                         if (gl == 0) {
-                            const int e = atomicAdd(&misc->fbcount, 1);
-                            fbant[e] = a;
-                            fbkey[e] = 0ull;
+                            const int qi = atomicAdd(qn, 1);
+                            qant[qi] = al;
+                            qc[qi] = c;
+                            pedge[al] = 0x80000000u | (uint32_t)qi;
                         }
                         continue;
                     }
                     float tv[V];
-                    if (!SPM) {
+                    if constexpr (!SPM) {
                         const float* trow = tau + (size_t)c * n;
 #pragma unroll
-                        for (int i = 0; i < V; ++i) tv[i] = unv[i] ? trow[nv[i]] : 0.0f;
+                        for (int i = 0; i < V; ++i) tv[i] = unv[i] ? __ldcg(trow + nv[i]) : 0.0f;
                     } else {
-                        const int32_t* ri = sidx + (size_t)c * s_slots;
-                        const float* rv = tau + (size_t)c * s_slots;
+                        const Rec R = rec(c);
 #pragma unroll
                         for (int i = 0; i < V; ++i) tv[i] = tau0;
+#pragma unroll 8
                         for (int q = 0; q < s_slots; ++q) {
-                            const int j = ri[q];
-                            const float t = rv[q];
+                            const int j = ld_i<RG>(R.idx + q);
+                            const float t = ld_f<RG>(R.val + q);
 #pragma unroll
                             for (int i = 0; i < V; ++i)
                                 if (nv[i] == j) tv[i] = t;
@@ -278,23 +396,22 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     const float q = unit24(x.x);
                     int kpick;
                     if (q < A.q0) {
-                        // exploitation: argmax of tau*eta^beta, ties -> lowest rank
-                        unsigned long long bk = 0ull;
+                        // exploitation: argmax of tau*eta^beta, ties -> lowest rank.
+                        // Non-negative floats order like their bit patterns.
+                        uint32_t mb = 0u;
 #pragma unroll
-                        for (int i = 0; i < V; ++i) {
-                            if (unv[i]) {
-                                const unsigned long long key =
-                                    ((unsigned long long)__float_as_uint(v[i]) << 32) |
-                                    (unsigned long long)(0xffffffffu - (uint32_t)(gl * V + i));
-                                bk = key > bk ? key : bk;
-                            }
-                        }
+                        for (int i = 0; i < V; ++i)
+                            if (unv[i]) mb = max(mb, __float_as_uint(v[i]));
 #pragma unroll
-                        for (int off = TPA / 2; off >= 1; off >>= 1) {
-                            const unsigned long long o = __shfl_xor_sync(gmask, bk, off, TPA);
-                            bk = o > bk ? o : bk;
-                        }
-                        kpick = (int)(0xffffffffu - (uint32_t)(bk & 0xffffffffull));
+                        for (int off = TPA / 2; off >= 1; off >>= 1)
+                            mb = max(mb, __shfl_xor_sync(gmask, mb, off, TPA));
+                        int first = -1;
+#pragma unroll
+                        for (int i = V - 1; i >= 0; --i)
+                            if (unv[i] && __float_as_uint(v[i]) == mb) first = i;
+                        const unsigned bf = __ballot_sync(gmask, first >= 0) & gmask;
+                        const int src = __ffs(bf) - 1 - gbase;
+                        kpick = src * V + __shfl_sync(gmask, first, src, TPA);
                     } else {
                         // exploration: roulette of Eq. 2 over a 32-position
                         // inclusive Hillis-Steele scan (offsets 1,2,4,8,16)
@@ -321,7 +438,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                                 }
 #pragma unroll
                                 for (int i = 0; i < V; ++i) {
-                                    if (i >= off) y[i] = __fadd_rn(P[i], P[(i - off + V) % V]);
+                                    if (i >= off) y[i] = __fadd_rn(P[i], P[i - off]);
                                     else y[i] = gl >= 1 ? __fadd_rn(P[i], prev[i]) : P[i];
                                 }
                             }
@@ -341,16 +458,15 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                         const unsigned bf = __ballot_sync(gmask, first >= 0) & gmask;
                         const unsigned bl = __ballot_sync(gmask, last >= 0) & gmask;
                         const unsigned bu = __ballot_sync(gmask, firstu >= 0) & gmask;
-                        const int base = lane & ~(TPA - 1);
                         if (bf) {
-                            const int src = __ffs(bf) - 1;
-                            kpick = (src - base) * V + __shfl_sync(gmask, first, src - base, TPA);
+                            const int src = __ffs(bf) - 1 - gbase;
+                            kpick = src * V + __shfl_sync(gmask, first, src, TPA);
                         } else if (bl) {
-                            const int src = 31 - __clz(bl);
-                            kpick = (src - base) * V + __shfl_sync(gmask, last, src - base, TPA);
+                            const int src = 31 - __clz(bl) - gbase;
+                            kpick = src * V + __shfl_sync(gmask, last, src, TPA);
                         } else {
-                            const int src = __ffs(bu) - 1;
-                            kpick = (src - base) * V + __shfl_sync(gmask, firstu, src - base, TPA);
+                            const int src = __ffs(bu) - 1 - gbase;
+                            kpick = src * V + __shfl_sync(gmask, firstu, src, TPA);
                         }
                     }
                     // broadcast the chosen node and its pheromone from the owning lane
@@ -363,198 +479,269 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     const int next = __shfl_sync(gmask, myn, owner, TPA);
                     const float tsel = __shfl_sync(gmask, myt, owner, TPA);
                     if (gl == 0) {
-                        s_nxt[a] = next;
-                        s_tsel[a] = tsel;
+                        s_nxt[al] = next;
+                        s_tsel[al] = tsel;
+                        pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
                         tours[(size_t)a * n + step] = next;
-                        vis_base[(size_t)a * W + (next >> 5)] |= 1u << (next & 31);
-                        if (upd) {
-                            const uint32_t lo = (uint32_t)min(c, next), hi = (uint32_t)max(c, next);
-                            s_slot[a] = edge_insert(ekey, ecnt, erep, A.H, lo * (uint32_t)n + hi, a,
-                                                    A.status);
-                        }
+                        vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
                     }
                 }
-                __syncthreads();
-
-                // Phase B: full scan for ants whose candidate set is empty
-                const int E = misc->fbcount;
-                if (E > 0) {
-                    for (int e = 0; e < E; ++e) {
-                        const int a = fbant[e];
-                        const int c = s_cur[a];
-                        const uint32_t* vis = vis_base + (size_t)a * W;
-                        const int2 pc = load_xy(xy, c);
-                        unsigned long long bk = 0ull;
-                        if (!SPM) {
-                            const float* trow = tau + (size_t)c * n;
-                            for (int j = tid; j < n; j += nthr) {
-                                if (visited(vis, j)) continue;
-                                const float p = __fmul_rn(trow[j], heuristic(euc2d(pc, load_xy(xy, j)), A.beta));
-                                const unsigned long long key =
-                                    ((unsigned long long)__float_as_uint(p) << 32) | (0xffffffffu - (uint32_t)j);
-                                bk = key > bk ? key : bk;
-                            }
-                        } else {
-                            const int32_t* ri = sidx + (size_t)c * s_slots;
-                            const float* rv = tau + (size_t)c * s_slots;
-                            for (int j = tid; j < n; j += nthr) {
-                                if (visited(vis, j)) continue;
-                                const float t = spm_read(ri, rv, s_slots, j, tau0);
-                                const float p = __fmul_rn(t, heuristic(euc2d(pc, load_xy(xy, j)), A.beta));
-                                const unsigned long long key =
-                                    ((unsigned long long)__float_as_uint(p) << 32) | (0xffffffffu - (uint32_t)j);
-                                bk = key > bk ? key : bk;
-                            }
-                        }
-#pragma unroll
-                        for (int off = 16; off >= 1; off >>= 1) {
-                            const unsigned long long o = __shfl_xor_sync(0xffffffffu, bk, off);
-                            bk = o > bk ? o : bk;
-                        }
-                        if (lane == 0 && bk != 0ull) atomicMax(&fbkey[e], bk);
-                    }
-                    __syncthreads();
-                    for (int e = tid; e < E; e += nthr) {
-                        const int a = fbant[e];
-                        const int c = s_cur[a];
-                        const unsigned long long bk = fbkey[e];
-                        const int next = (int)(0xffffffffu - (uint32_t)(bk & 0xffffffffull));
-                        if (bk == 0ull || next < 0 || next >= n) { atomicExch(A.status, 4); continue; }
-                        s_nxt[a] = next;
-                        if (!SPM) {
-                            s_tsel[a] = tau[(size_t)c * n + next];
-                        } else {
-                            s_tsel[a] = 0.0f;
-                        }
-                        tours[(size_t)a * n + step] = next;
-                        vis_base[(size_t)a * W + (next >> 5)] |= 1u << (next & 31);
-                        if (upd) {
-                            const uint32_t lo = (uint32_t)min(c, next), hi = (uint32_t)max(c, next);
-                            s_slot[a] = edge_insert(ekey, ecnt, erep, A.H, lo * (uint32_t)n + hi, a,
-                                                    A.status);
-                        }
-                    }
-                    if (tid == 0) {
-                        n_fb += (unsigned long long)E;
-                        misc->fbcount = 0;
-                    }
-                    __syncthreads();
-                }
-                if (tid == 0) n_sel += (unsigned long long)m;
             } else {
                 // closing edges (step n): last node back to the first
-                for (int a = tid; a < m; a += nthr) {
-                    const int c = s_cur[a], next = s_start[a];
-                    s_nxt[a] = next;
-                    if (upd) {
-                        if (!SPM) s_tsel[a] = tau[(size_t)c * n + next];
-                        const uint32_t lo = (uint32_t)min(c, next), hi = (uint32_t)max(c, next);
-                        s_slot[a] = edge_insert(ekey, ecnt, erep, A.H, lo * (uint32_t)n + hi, a, A.status);
-                    }
+                for (int al = tid; al < ml; al += nthr) {
+                    const int c = s_cur[al], next = s_start[al];
+                    s_nxt[al] = next;
+                    pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
+                    if (upd && !SPM) s_tsel[al] = __ldcg(tau + (size_t)c * n + next);
                 }
-                __syncthreads();
             }
+            cluster.sync();   // the step's edges and queues are visible cluster-wide
 
-            // Phase C: folded local update of the step's distinct edges (thread a = ant a)
-            if (!SPM) {
-                if (tid < m) {
-                    const int a = tid;
-                    const int u = s_cur[a], v = s_nxt[a];
-                    if (upd) {
-                        const int slot = s_slot[a];
-                        if (erep[slot] == a) {
-                            const int k = ecnt[slot];
-                            const float t2 = local_rule(s_tsel[a], tau0, sP[k]);
-                            tau[(size_t)u * n + v] = t2;
-                            tau[(size_t)v * n + u] = t2;
-                            ekey[slot] = kEmpty;
-                            ecnt[slot] = 0;
-                            erep[slot] = 0x7fffffff;
+            // Phase B: the cluster's queued ants, argmax over all unvisited nodes
+            if (tid == 0) {
+                int acc = 0;
+                misc->qoff[0] = 0;
+                for (int r = 0; r < C; ++r) {
+                    acc += cluster.map_shared_rank(&misc->qn[step & 1], r)[0];
+                    misc->qoff[r + 1] = acc;
+                }
+            }
+            __syncthreads();
+            const int Q = misc->qoff[C];
+            if (Q > 0) {
+                // entry e of the cluster: owner CTA, owner's ant, current node
+                if (tid < Q) {
+                    int r = 0;
+                    while (misc->qoff[r + 1] <= tid) ++r;
+                    const int qi = tid - misc->qoff[r];
+                    qpart[tid] = 0ull;
+                    eqown[tid] = r;
+                    eqal[tid] = cluster.map_shared_rank(qant, r)[qi];
+                    const int c = cluster.map_shared_rank(qc, r)[qi];
+                    eqc[tid] = c;
+                    if constexpr (SPM) {
+                        const Rec R = rec(c);
+                        for (int q2 = 0; q2 < s_slots; ++q2) {
+                            fri[tid * s_slots + q2] = ld_i<RG>(R.idx + q2);
+                            frv[tid * s_slots + q2] = ld_f<RG>(R.val + q2);
                         }
                     }
-                    s_cur[a] = v;
                 }
                 __syncthreads();
-            } else {
-                bool p0 = false, p1 = false;
-                int u = 0, v = 0, rs0 = 0, rs1 = 0;
-                float coef = 0.0f;
-                if (tid < m) {
-                    const int a = tid;
-                    u = s_cur[a];
-                    v = s_nxt[a];
-                    if (upd) {
-                        const int slot = s_slot[a];
-                        if (erep[slot] == a) {
-                            coef = sP[ecnt[slot]];
-                            rs0 = rec_insert(rkey, A.H2, (uint32_t)u, A.status);
-                            rs1 = rec_insert(rkey, A.H2, (uint32_t)v, A.status);
-                            p0 = p1 = true;
-                            ekey[slot] = kEmpty;
-                            ecnt[slot] = 0;
-                            erep[slot] = 0x7fffffff;
+                const int span = (n + C - 1) / C;
+                const int jlo = rank * span, jhi = min(n, jlo + span);
+                // warps are split among the entries so that all entries are
+                // scanned at once: with Q <= warps entry e gets the warps e,
+                // e+Q, ... (nwarps/Q of them); otherwise one warp per entry
+                const int nwarps = nthr >> 5, warp = tid >> 5;
+                const int wpe = Q <= nwarps ? nwarps / Q : 1;
+                for (int e = Q <= nwarps ? warp % Q : warp; e < Q; e += nwarps) {
+                    const int wi = Q <= nwarps ? warp / Q : 0;
+                    if (wi >= wpe) break;
+                    const int r = eqown[e], c = eqc[e];
+                    const uint32_t* vis = vis_of(r, eqal[e]);
+                    const float* trow = tau + (size_t)c * n;
+                    const float* hrow = hw ? hw + (size_t)c * n : nullptr;
+                    const int2 pc = xy[c];
+                    unsigned long long key = 0ull;
+#pragma unroll 2
+                    for (int j = jlo + wi * 32 + lane; j < jhi; j += wpe * 32) {
+                        // the loads are issued before the visited test
+                        const uint32_t word = vis[j >> 5];
+                        float t;
+                        if constexpr (SPM) {
+                            t = tau0;
+                            for (int q2 = 0; q2 < s_slots; ++q2)
+                                if (fri[e * s_slots + q2] == j) t = frv[e * s_slots + q2];
+                        } else {
+                            t = __ldcg(trow + j);
                         }
+                        const float h = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
+                        if ((word >> (j & 31)) & 1u) continue;
+                        const unsigned long long k2 = pack_pj(__fmul_rn(t, h), j);
+                        key = k2 > key ? k2 : key;
                     }
-                    s_cur[a] = v;
+                    key = warp_max_u64(key);
+                    if (lane == 0 && key != 0ull) atomicMax(&qpart[e], key);
+                    if (Q <= nwarps) break;
                 }
-                int round = 0;
-                bool used0 = p0, used1 = p1;
-                // each round retires the lowest pending event of every record, so
-                // at most 2m rounds are needed; the bound only guards against a bug
-                while (__syncthreads_or(p0 || p1)) {
-                    if (round > 2 * m + 2) {
-                        if (tid == 0) atomicExch(A.status, 5);
-                        p0 = p1 = false;
+                cluster.sync();   // every CTA's partial argmax is final
+                // owners finish their queued ants
+                const int E = misc->qoff[rank + 1] - misc->qoff[rank];
+                for (int qi = tid; qi < E; qi += nthr) {
+                    const int al = qant[qi], c = qc[qi];
+                    const unsigned long long key = cluster_max_entry(cluster, qpart, misc->qoff[rank] + qi, C);
+                    const int next = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+                    if (key == 0ull || next < 0 || next >= n) {
+                        atomicExch(A.status, 4);
                         continue;
                     }
-                    uint32_t* rm = rmin + (round & 1) * A.H2;
-                    const uint32_t o0 = 2u * (uint32_t)tid, o1 = o0 + 1u;
-                    if (p0) atomicMin(&rm[rs0], o0);
-                    if (p1) atomicMin(&rm[rs1], o1);
-                    __syncthreads();
-                    if (p0 && rm[rs0] == o0) {
-                        const bool hit = spm_apply(sidx + (size_t)u * s_slots, tau + (size_t)u * s_slots,
-                                                   stail + u, s_slots, v, tau0, 0, coef, 0.0f);
-                        if (hit) ++n_hit; else ++n_miss;
-                        rm[rs0] = kEmpty;
-                        p0 = false;
-                    }
-                    if (p1 && rm[rs1] == o1) {
-                        const bool hit = spm_apply(sidx + (size_t)v * s_slots, tau + (size_t)v * s_slots,
-                                                   stail + v, s_slots, u, tau0, 0, coef, 0.0f);
-                        if (hit) ++n_hit; else ++n_miss;
-                        rm[rs1] = kEmpty;
-                        p1 = false;
-                    }
-                    ++round;
+                    s_nxt[al] = next;
+                    if constexpr (!SPM) s_tsel[al] = __ldcg(tau + (size_t)c * n + next);
+                    tours[(size_t)(a0 + al) * n + step] = next;
+                    vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
                 }
-                if (used0) rkey[rs0] = kEmpty;
-                if (used1) rkey[rs1] = kEmpty;
-                // the next writer of rkey is the next step's phase C, two barriers away
+                if (tid == 0) n_fb += (unsigned long long)E;
             }
+
+            // Phase C: folded local update of the step's distinct edges
+            if (upd) {
+                // every CTA gathers all m edges (one thread per ant: m <= nthr)
+                if (tid == 0) misc->nrel = 0;
+                if (tid < m) {
+                    const int a = tid;
+                    const int r = a / mc;
+                    const uint32_t e = cluster.map_shared_rank(pedge, r)[a - r * mc];
+                    int u, v;
+                    if (e & 0x80000000u) {
+                        const int qi = (int)(e & 0xffffu);
+                        const unsigned long long key = cluster_max_entry(cluster, qpart, misc->qoff[r] + qi, C);
+                        u = cluster.map_shared_rank(qc, r)[qi];
+                        v = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+                    } else {
+                        u = (int)(e >> 16);
+                        v = (int)(e & 0xffffu);
+                    }
+                    gkey[a] = (uint32_t)min(u, v) * (uint32_t)n + (uint32_t)max(u, v);
+                    gu[a] = u;
+                    gv[a] = v;
+                }
+                __syncthreads();
+                // This CTA only needs the edges it writes: on the matrix its own
+                // ants' edges, on the SPM the edges that touch one of its records
+                // (their events are the only ones replayed here).
+                if (tid < m) {
+                    const int a = tid;
+                    const bool rel = SPM ? ((gu[a] % C) == rank || (gv[a] % C) == rank)
+                                         : (a >= a0 && a < a0 + ml);
+                    if (rel) eqal[atomicAdd(&misc->nrel, 1)] = a;   // eqal is free again here
+                }
+                __syncthreads();
+                const int NR = misc->nrel;
+                // k = ants on the same undirected edge, representative = lowest
+                // ant; T threads per relevant edge compare it with every T-th edge
+                // (whole warps take part so that the segmented shuffles are valid)
+                int T = 1;
+                while (T < 32 && 2 * T * NR <= nthr) T *= 2;
+                const int tm = (T * NR + 31) & ~31;
+                if (tid < tm) {
+                    const int i = tid / T, part = tid - i * T;
+                    const bool valid = i < NR;
+                    const int a = valid ? eqal[i] : 0;
+                    const uint32_t key = gkey[a];
+                    int cnt = 0, rep = a;
+                    if (valid) {
+                        for (int bb = part; bb < m; bb += T) {
+                            if (gkey[bb] == key) {
+                                ++cnt;
+                                rep = min(rep, bb);
+                            }
+                        }
+                    }
+                    cnt = seg_sum(cnt, T);
+                    rep = seg_min(rep, T);
+                    if (valid && part == 0) {
+                        grep[a] = rep;
+                        gcnt[a] = cnt;
+                        ev0[a] = rep == a ? gu[a] : -1;
+                        ev1[a] = rep == a ? gv[a] : -1;
+                    }
+                }
+                __syncthreads();
+                if constexpr (!SPM) {
+                    // the CTA of the lowest ant on an edge writes both halves
+                    for (int al = tid; al < ml; al += nthr) {
+                        const int a = a0 + al;
+                        if (grep[a] == a) {
+                            const float t2 = local_rule(s_tsel[al], tau0, sP[gcnt[a]]);
+                            const int u = gu[a], v = gv[a];
+                            tau[(size_t)u * n + v] = t2;
+                            tau[(size_t)v * n + u] = t2;
+                        }
+                    }
+                } else {
+                    // record r belongs to CTA r mod C. An event's rank among the
+                    // events on its record, in (ant, side) order, is its round.
+                    bool p0 = false, p1 = false;
+                    int u = 0, v = 0, r0 = 0, r1 = 0;
+                    float coef = 0.0f;
+                    if (tid < tm) {
+                        const int i = tid / T, part = tid - i * T;
+                        const bool valid = i < NR;
+                        const int a = valid ? eqal[i] : 0;
+                        const bool isrep = valid && grep[a] == a;
+                        u = gu[a];
+                        v = gv[a];
+                        const bool own0 = isrep && (u % C) == rank;
+                        const bool own1 = isrep && (v % C) == rank;
+                        if (own0 || own1) {
+                            // earlier events (lower ant) on the same records; every
+                            // such event belongs to a relevant edge
+                            for (int jj = part; jj < NR; jj += T) {
+                                const int bb = eqal[jj];
+                                if (bb >= a) continue;
+                                const int x0 = ev0[bb], x1 = ev1[bb];
+                                r0 += (x0 == u) + (x1 == u);
+                                r1 += (x0 == v) + (x1 == v);
+                            }
+                        }
+                        r0 = seg_sum(r0, T);
+                        r1 = seg_sum(r1, T);
+                        if (part == 0 && isrep) {
+                            p0 = own0;
+                            p1 = own1;
+                            coef = sP[gcnt[a]];
+                        }
+                    }
+                    for (int t = 0;; ++t) {
+                        if (p0 && r0 == t) {
+                            const bool hit = spm_apply<RG>(rec(u), s_slots, v, tau0, 0, coef, 0.0f);
+                            if (hit) ++n_hit; else ++n_miss;
+                            p0 = false;
+                        }
+                        if (p1 && r1 == t) {
+                            const bool hit = spm_apply<RG>(rec(v), s_slots, u, tau0, 0, coef, 0.0f);
+                            if (hit) ++n_hit; else ++n_miss;
+                            p1 = false;
+                        }
+                        if (!__syncthreads_or(p0 || p1)) break;
+                        if (t > 2 * m + 2) {   // ranks are < 2m: only a bug gets here
+                            if (tid == 0) atomicExch(A.status, 5);
+                            break;
+                        }
+                    }
+                }
+            }
+            for (int al = tid; al < ml; al += nthr) s_cur[al] = s_nxt[al];
+            // the queue counter of the next step was last read before the
+            // previous barrier, so it can be cleared now
+            if (tid == 0) misc->qn[(step + 1) & 1] = 0;
+            cluster.sync();
         }
 
         // ---- tour lengths (Alg. 1 select_best), one group per ant
-        for (int a = group; a < m; a += ngroups) {
+        for (int al = group; al < ml; al += ngroups) {
+            const int a = a0 + al;
             const int32_t* t = tours + (size_t)a * n;
             long long sum = 0;
             for (int i = gl; i < n; i += TPA) {
                 const int x = t[i], y = t[i + 1 < n ? i + 1 : 0];
-                sum += euc2d(load_xy(xy, x), load_xy(xy, y));
+                sum += euc2d(xy[x], xy[y]);
             }
 #pragma unroll
             for (int off = TPA / 2; off >= 1; off >>= 1) sum += __shfl_xor_sync(gmask, sum, off, TPA);
             if (gl == 0) {
-                s_len[a] = sum;
+                s_len[al] = sum;
                 A.lens[D.ant_off + a] = sum;
             }
         }
-        __syncthreads();
+        cluster.sync();
         if (tid < 32) {
             long long bl = 0x7fffffffffffffffll;
             int ba = 0x7fffffff;
             for (int a = tid; a < m; a += 32) {
-                const long long l = s_len[a];
+                const int r = a / mc;
+                const long long l = cluster.map_shared_rank(s_len, r)[a - r * mc];
                 if (l < bl || (l == bl && a < ba)) { bl = l; ba = a; }
             }
 #pragma unroll
@@ -571,108 +758,163 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         }
         __syncthreads();
         if (misc->improved) {
+            // the cluster copies the new best tour, one slice per CTA
             const int32_t* src = tours + (size_t)misc->bestant * n;
-            for (int i = tid; i < n; i += nthr) best[i] = src[i];
-            __syncthreads();
+            for (int i = rank * nthr + tid; i < n; i += C * nthr) best[i] = __ldcg(src + i);
         }
+        cluster.sync();
 
         // ---- global update on the best-so-far tour (eq. global_update)
         const long long Lgb = misc->best_len;
         const float delta = __double2float_rn(1.0 / (double)Lgb);
-        if (!SPM) {
-            for (int i = tid; i < n; i += nthr) {
-                const int u = best[i], v = best[i + 1 < n ? i + 1 : 0];
-                const float t2 = global_rule(tau[(size_t)u * n + v], delta, A.rho);
+        if constexpr (!SPM) {
+            for (int i = rank * nthr + tid; i < n; i += C * nthr) {
+                const int u = __ldcg(best + i), v = __ldcg(best + (i + 1 < n ? i + 1 : 0));
+                const float t2 = global_rule(__ldcg(tau + (size_t)u * n + v), delta, A.rho);
                 tau[(size_t)u * n + v] = t2;
                 tau[(size_t)v * n + u] = t2;
             }
         } else {
-            // record best[i] sees, in tour order, the edge (best[i-1], best[i])
-            // then (best[i], best[i+1]); record best[0] sees edge 0 then edge n-1
+            // record best[i] (owned by CTA best[i] mod C) sees, in tour order, the
+            // edge (best[i-1], best[i]) then (best[i], best[i+1]); record best[0]
+            // sees edge 0 then edge n-1
             for (int i = tid; i < n; i += nthr) {
-                const int r = best[i];
-                const int prev = best[i > 0 ? i - 1 : n - 1];
-                const int nxt = best[i + 1 < n ? i + 1 : 0];
+                const int r = __ldcg(best + i);
+                if (r % C != rank) continue;
+                const int prev = __ldcg(best + (i > 0 ? i - 1 : n - 1));
+                const int nxt = __ldcg(best + (i + 1 < n ? i + 1 : 0));
                 const int first = i > 0 ? prev : nxt;
                 const int second = i > 0 ? nxt : prev;
-                int32_t* ri = sidx + (size_t)r * s_slots;
-                float* rv = tau + (size_t)r * s_slots;
-                bool h = spm_apply(ri, rv, stail + r, s_slots, first, tau0, 1, A.rho, delta);
+                const Rec R = rec(r);
+                bool h = spm_apply<RG>(R, s_slots, first, tau0, 1, A.rho, delta);
                 if (h) ++n_hit; else ++n_miss;
-                h = spm_apply(ri, rv, stail + r, s_slots, second, tau0, 1, A.rho, delta);
+                h = spm_apply<RG>(R, s_slots, second, tau0, 1, A.rho, delta);
                 if (h) ++n_hit; else ++n_miss;
             }
-        }
-        if (SPM) {
             atomicAdd(&misc->stat[2], n_hit);
             atomicAdd(&misc->stat[3], n_miss);
         }
         __syncthreads();
-        if (tid == 0) {
-            A.best_len[b] = misc->best_len;
-            A.iteration[b] = misc->iteration + 1;
-            unsigned long long* st = A.stats + 4 * (size_t)b;
-            st[0] += n_fb;
-            st[1] += n_sel;
-            st[2] += misc->stat[2];
-            st[3] += misc->stat[3];
+        if constexpr (MODE == 2) {
+            // write this CTA's records back to global memory
+            for (int li = tid; li < A.nrec; li += nthr) {
+                const int r = rank + li * C;
+                if (r >= n) continue;
+                for (int q = 0; q < s_slots; ++q) {
+                    sidx[(size_t)r * s_slots + q] = ridx_s[li * s_slots + q];
+                    tau[(size_t)r * s_slots + q] = rval_s[li * s_slots + q];
+                }
+                stail[r] = rtail_s[li];
+            }
         }
-        __syncthreads();
+        if (tid == 0) {
+            unsigned long long* st = A.stats + 4 * (size_t)b;
+            atomicAdd(st + 0, n_fb);
+            if (rank == 0) atomicAdd(st + 1, (unsigned long long)m * (unsigned long long)(n - 1));
+            atomicAdd(st + 2, misc->stat[2]);
+            atomicAdd(st + 3, misc->stat[3]);
+            if (rank == 0) {
+                A.best_len[b] = misc->best_len;
+                A.iteration[b] = misc->iteration + 1;
+            }
+        }
+        cluster.sync();
     }
 }
 
-template <int TPA, bool SPM>
+template <int TPA, int MODE>
 static void* kernel_ptr()
 {
-    return reinterpret_cast<void*>(construct_kernel<TPA, SPM>);
+    return reinterpret_cast<void*>(construct_kernel<TPA, MODE>);
 }
 
-static void* select_kernel(int tpa, bool spm)
+template <int MODE>
+static void* select_tpa(int tpa)
 {
     switch (tpa) {
-    case 8: return spm ? kernel_ptr<8, true>() : kernel_ptr<8, false>();
-    case 16: return spm ? kernel_ptr<16, true>() : kernel_ptr<16, false>();
-    case 32: return spm ? kernel_ptr<32, true>() : kernel_ptr<32, false>();
+    case 4: return kernel_ptr<4, MODE>();
+    case 8: return kernel_ptr<8, MODE>();
+    case 16: return kernel_ptr<16, MODE>();
+    case 32: return kernel_ptr<32, MODE>();
     default: return nullptr;
     }
 }
 
-// Raises the kernel's dynamic shared-memory limit to at least `smem` (outside
-// any stream capture). The limit is a per-function setting shared by every
-// context in the process, so it is only ever raised: lowering it would make
-// the launches of an existing context with a larger layout fail.
-cudaError_t prepare_construct(int tpa, bool spm, size_t smem)
+static void* select_kernel(int tpa, int mode)
+{
+    switch (mode) {
+    case 0: return select_tpa<0>(tpa);
+    case 1: return select_tpa<1>(tpa);
+    case 2: return select_tpa<2>(tpa);
+    default: return nullptr;
+    }
+}
+
+// Raises the kernel's dynamic shared-memory limit to at least `smem` and
+// allows clusters above 8 CTAs (outside any stream capture). The limit is a
+// per-function setting shared by every context in the process, so it is only
+// ever raised: lowering it would make the launches of an existing context
+// with a larger layout fail.
+cudaError_t prepare_construct(int tpa, int mode, size_t smem)
 {
     static std::mutex mu;
-    void* k = select_kernel(tpa, spm);
+    void* k = select_kernel(tpa, mode);
     if (!k) return cudaErrorInvalidValue;
     std::lock_guard<std::mutex> lock(mu);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k);
+    e = cudaFuncGetAttributes(&fa, k);
     if (e != cudaSuccess) return e;
     if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int construct_occupancy(int tpa, bool spm, int block, size_t smem)
+// Clusters of `csize` CTAs that can be resident at once (0 if none fits).
+int construct_occupancy(int tpa, int mode, int block, size_t smem, int csize)
 {
-    void* k = select_kernel(tpa, spm);
-    int occ = 0;
-    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, smem) != cudaSuccess) {
+    void* k = select_kernel(tpa, mode);
+    if (!k) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = csize;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    return occ;
+    return nclusters;
 }
 
-// Stream-ordered launch of one iteration; safe inside a stream capture.
-cudaError_t launch_construct(const ConstructArgs& A, int tpa, bool spm, int grid, int block,
-                             size_t smem, cudaStream_t stream)
+// Stream-ordered launch of one iteration on clusters of `csize` CTAs; safe
+// inside a stream capture. grid must be a multiple of csize.
+cudaError_t launch_construct(const ConstructArgs& A, int tpa, int mode, int grid, int block,
+                             size_t smem, int csize, cudaStream_t stream)
 {
-    void* k = select_kernel(tpa, spm);
+    void* k = select_kernel(tpa, mode);
     if (!k) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = csize;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
     void* args[] = {const_cast<ConstructArgs*>(&A)};
-    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, stream);
+    return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 }  // namespace acs

@@ -23,6 +23,7 @@ struct InstDesc {
     int64_t tour_off;   // tours[tour_off + a*n + step]
     int64_t ant_off;    // lens[ant_off + a]
     int64_t vis_off;    // global visited words (when not in shared memory)
+    int64_t hw_off;     // heuristic matrix hw[hw_off + c*n + j] (when present)
     float tau0;
     int32_t pad;
 };
@@ -37,6 +38,7 @@ struct ConstructArgs {
     const int32_t* xy;
     const int32_t* nn;        // [rows][32], -1 padded
     const float* w;           // [rows][32], 0 padded
+    const float* hw;          // heuristic matrix (same offsets as the matrix), or null
     float* tau;               // matrix entries, or SPM trail values
     int32_t* spm_idx;         // SPM neighbour per slot
     int32_t* spm_tail;        // SPM tail per node
@@ -53,39 +55,55 @@ struct ConstructArgs {
     int32_t beta, s, period;
     uint32_t key0, key1;
     int32_t vis_in_smem, xy_in_smem, max_n;
-    int32_t H, H2;            // edge / record hash sizes (powers of two)
+    int32_t mc;               // ants per CTA of a cluster = ceil(m / cluster size)
+    int32_t nrec;             // SPM records per CTA in shared memory (0 = global)
 };
 
 // Shared-memory carve of the construct kernel; the same arithmetic runs on
 // the host (to size the launch) and on the device (to place the arrays).
+// mc = ants owned by one CTA of the cluster, m = ants of the instance.
 struct SmemLayout {
-    uint32_t P, cur, start, nxt, slot, tsel, len, ekey, ecnt, erep, rkey, rmin,
-        fbant, fbkey, misc, vis, xy, total;
+    uint32_t P, cur, start, nxt, tsel, len, pedge, qant, qc, qpart, eqc, eqown, eqal, gkey, gu,
+        gv, grep, gcnt, ev0, ev1, fri, frv, misc, ridx, rval, rtail, vis, xy, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-__host__ __device__ inline SmemLayout smem_layout(int m, int H, int H2, int W, int max_n,
+// mc = ants owned by one CTA of the cluster, m = ants of the instance, nrec =
+// SPM records held in shared memory by one CTA (0 = records stay in global
+// memory), s = SPM slots per record (0 for the matrix).
+__host__ __device__ inline SmemLayout smem_layout(int m, int mc, int nrec, int s, int W, int max_n,
                                                   bool vis_in_smem, bool xy_in_smem)
 {
     SmemLayout L;
     uint32_t o = 0;
     L.P = o;     o = align16(o + 4u * (m + 1));
-    L.cur = o;   o = align16(o + 4u * m);
-    L.start = o; o = align16(o + 4u * m);
-    L.nxt = o;   o = align16(o + 4u * m);
-    L.slot = o;  o = align16(o + 4u * m);
-    L.tsel = o;  o = align16(o + 4u * m);
-    L.len = o;   o = align16(o + 8u * m);
-    L.ekey = o;  o = align16(o + 4u * H);
-    L.ecnt = o;  o = align16(o + 4u * H);
-    L.erep = o;  o = align16(o + 4u * H);
-    L.rkey = o;  o = align16(o + 4u * H2);
-    L.rmin = o;  o = align16(o + 8u * H2);
-    L.fbant = o; o = align16(o + 4u * m);
-    L.fbkey = o; o = align16(o + 8u * m);
-    L.misc = o;  o = align16(o + 512u);
-    L.vis = o;   if (vis_in_smem) o = align16(o + 4u * (uint32_t)m * (uint32_t)W);
+    L.cur = o;   o = align16(o + 4u * mc);
+    L.start = o; o = align16(o + 4u * mc);
+    L.nxt = o;   o = align16(o + 4u * mc);
+    L.tsel = o;  o = align16(o + 4u * mc);
+    L.len = o;   o = align16(o + 8u * mc);
+    L.pedge = o; o = align16(o + 4u * mc);
+    L.qant = o;  o = align16(o + 4u * mc);
+    L.qc = o;    o = align16(o + 4u * mc);
+    L.qpart = o; o = align16(o + 8u * m);
+    L.eqc = o;   o = align16(o + 4u * m);
+    L.eqown = o; o = align16(o + 4u * m);
+    L.eqal = o;  o = align16(o + 4u * m);
+    L.gkey = o;  o = align16(o + 4u * m);
+    L.gu = o;    o = align16(o + 4u * m);
+    L.gv = o;    o = align16(o + 4u * m);
+    L.grep = o;  o = align16(o + 4u * m);
+    L.gcnt = o;  o = align16(o + 4u * m);
+    L.ev0 = o;   o = align16(o + 4u * m);
+    L.ev1 = o;   o = align16(o + 4u * m);
+    L.fri = o;   o = align16(o + 4u * (uint32_t)m * (uint32_t)s);
+    L.frv = o;   o = align16(o + 4u * (uint32_t)m * (uint32_t)s);
+    L.misc = o;  o = align16(o + 256u);
+    L.ridx = o;  o = align16(o + 4u * (uint32_t)nrec * (uint32_t)s);
+    L.rval = o;  o = align16(o + 4u * (uint32_t)nrec * (uint32_t)s);
+    L.rtail = o; o = align16(o + 4u * (uint32_t)nrec);
+    L.vis = o;   if (vis_in_smem) o = align16(o + 4u * (uint32_t)mc * (uint32_t)W);
     L.xy = o;    if (xy_in_smem) o = align16(o + 8u * (uint32_t)max_n);
     L.total = o;
     return L;

@@ -21,9 +21,9 @@
 #include "acs_internal.cuh"
 
 namespace acs {
-cudaError_t prepare_construct(int tpa, bool spm, size_t smem);
-cudaError_t launch_construct(const ConstructArgs& A, int tpa, bool spm, int grid, int block,
-                             size_t smem, cudaStream_t stream);
+cudaError_t prepare_construct(int tpa, int mode, size_t smem);
+cudaError_t launch_construct(const ConstructArgs& A, int tpa, int mode, int grid, int block,
+                             size_t smem, int csize, cudaStream_t stream);
 }  // namespace acs
 
 using namespace acs;
@@ -69,13 +69,6 @@ cudaError_t scratch_address(unsigned char** out)
     }
     *out = g_addr[dev];
     return cudaSuccess;
-}
-
-int next_pow2(int x)
-{
-    int v = 1;
-    while (v < x) v <<= 1;
-    return v;
 }
 
 }  // namespace
@@ -162,16 +155,16 @@ extern "C" acs_status acs_iterate_noalloc(const int32_t* dev_coords, int32_t n,
     A.vis_in_smem = 0;
     A.xy_in_smem = 0;
     A.max_n = n;
-    A.H = next_pow2(2 * m) < 64 ? 64 : next_pow2(2 * m);
-    A.H2 = next_pow2(4 * m) < 64 ? 64 : next_pow2(4 * m);
-    const SmemLayout L = smem_layout(m, A.H, A.H2, W, n, false, false);
+    A.mc = m;
+    A.nrec = 0;
+    const SmemLayout L = smem_layout(m, m, 0, 0, W, n, false, false);
     const int tpa = 8;
     int block = m * tpa < 64 ? 64 : (m * tpa > 1024 ? 1024 : m * tpa);
     block = (block + 31) / 32 * 32;
     if (block < m) block = (m + 31) / 32 * 32;
-    e = prepare_construct(tpa, false, L.total);
+    e = prepare_construct(tpa, 0, L.total);
     if (e != cudaSuccess) return ACS_ECUDA;
-    e = launch_construct(A, tpa, false, 1, block, L.total, st);
+    e = launch_construct(A, tpa, 0, 1, block, L.total, 1, st);
     if (e != cudaSuccess) return ACS_ECUDA;
 
     int32_t status = 0;

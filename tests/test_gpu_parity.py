@@ -81,6 +81,11 @@ EDGE_CASES = [
     dict(n=65, m=64, cl=16, local_period=3, q0=0.3),
     dict(n=65, m=9, cl=1, q0=1.0, beta=0),
     dict(n=100, m=70, cl=10, q0=0.0),
+    # small candidate lists: many full-scan fallbacks per step, queued by
+    # several CTAs of a cluster at once
+    dict(n=300, m=48, cl=4, q0=0.9),
+    dict(n=300, m=48, cl=4, beta=0),
+    dict(n=520, m=20, cl=2, q0=0.5),
 ]
 
 
@@ -158,6 +163,80 @@ def test_contexts_of_different_sizes_interleaved(oracle_mod):
         ra.run(1)
     assert_same_state(ga, ra, 0)
     assert_same_state(gb, rb, 0)
+
+
+@pytest.mark.parametrize("tpa", [4, 8, 16, 32])
+@pytest.mark.parametrize("memory", [0, 1])
+def test_threads_per_ant_variants_are_identical(oracle_mod, tpa, memory):
+    xy = instances.clustered(700, seed=12)
+    gpu, ref = _pair(xy, memory=memory, m=96, cl=32, spm_slots=8, q0=0.8, seed=4)
+    gpu.set_threads_per_ant(tpa)
+    for _ in range(2):
+        gpu.run(1)
+        ref.run(1)
+    assert_same_state(gpu, ref, memory)
+
+
+@pytest.mark.parametrize("tpa", [4, 32])
+@pytest.mark.parametrize("case", [dict(n=33, m=40, cl=32, local_period=2),
+                                  dict(n=300, m=48, cl=4, beta=0),
+                                  dict(n=65, m=9, cl=1, q0=1.0, beta=0)])
+def test_edge_cases_other_widths(oracle_mod, tpa, case):
+    case = dict(case)
+    n = case.pop("n")
+    xy = instances.uniform(n, side=1000, seed=n)
+    for memory in (0, 1):
+        gpu, ref = _pair(xy, memory=memory, spm_slots=3, seed=5, **case)
+        gpu.set_threads_per_ant(tpa)
+        for _ in range(3):
+            gpu.run(1)
+            ref.run(1)
+        assert_same_state(gpu, ref, memory)
+
+
+@pytest.mark.parametrize("csize", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("memory", [0, 1])
+def test_cluster_sizes_are_identical(oracle_mod, csize, memory):
+    # one instance shared by csize CTAs exchanging edges through DSMEM
+    xy = instances.clustered(700, seed=14)
+    gpu, ref = _pair(xy, memory=memory, m=96, cl=32, spm_slots=8, q0=0.8, seed=9)
+    try:
+        gpu.set_cluster_size(csize)
+    except acs.AcsError as e:
+        if csize == 16 and e.status == acs.ACS_EINVAL:
+            pytest.skip("16-CTA clusters cannot be scheduled for this layout")
+        raise
+    assert gpu.cluster_size == csize
+    for _ in range(2):
+        gpu.run(1)
+        ref.run(1)
+    assert_same_state(gpu, ref, memory)
+
+
+def test_uneven_ant_split_over_cluster(oracle_mod):
+    # m not a multiple of the cluster size: the last CTA owns fewer ants
+    xy = instances.uniform(260, seed=15)
+    for memory in (0, 1):
+        gpu, ref = _pair(xy, memory=memory, m=37, cl=16, spm_slots=4, q0=0.6, seed=10)
+        gpu.set_cluster_size(8)
+        gpu.set_threads_per_ant(16)
+        for _ in range(3):
+            gpu.run(1)
+            ref.run(1)
+        assert_same_state(gpu, ref, memory)
+
+
+def test_autotune_keeps_state(oracle_mod):
+    xy = instances.clustered(500, seed=13)
+    gpu, ref = _pair(xy, m=64, cl=32, seed=6)
+    gpu.run(1)
+    ref.run(1)
+    tpa, cs = gpu.autotune(2)
+    assert tpa in (4, 8, 16, 32) and cs in (1, 2, 4, 8, 16) and gpu.iteration == 1
+    assert gpu.threads_per_ant == tpa and gpu.cluster_size == cs
+    gpu.run(2)
+    ref.run(2)
+    assert_same_state(gpu, ref, 0)
 
 
 def test_repeatable_bits(oracle_mod):
