@@ -182,18 +182,28 @@ __device__ __forceinline__ int seg_min(int v, int T)
     return v;
 }
 
-// Maximum of entry `ent` over the C CTAs' partial results (C <= 16): the
-// loads are independent, so they are all issued before the first use.
+// Bring the line holding p into L2 (no register result, no L1 fill: other SMs
+// may write the line before it is read).
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Maximum of entry `ent` over the C CTAs' partial results (C <= 16), loaded
+// four at a time.
 __device__ __forceinline__ unsigned long long cluster_max_entry(cg::cluster_group& cluster,
                                                                 unsigned long long* part, int ent,
                                                                 int C)
 {
-    unsigned long long k[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) k[r] = r < C ? cluster.map_shared_rank(part, r)[ent] : 0ull;
     unsigned long long key = 0ull;
+    for (int r0 = 0; r0 < C; r0 += 4) {
+        unsigned long long k[4];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) key = k[r] > key ? k[r] : key;
+        for (int i = 0; i < 4; ++i)
+            k[i] = r0 + i < C ? cluster.map_shared_rank(part, r0 + i)[ent] : 0ull;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) key = k[i] > key ? k[i] : key;
+    }
     return key;
 }
 
@@ -351,6 +361,9 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     float wv[V];
                     load_row<V>(nn_rows + (size_t)c * 32 + gl * V, w_rows + (size_t)c * 32 + gl * V,
                                 nv, wv);
+                    // drawn here so that the rounds overlap the loads' latency
+                    const uint4 x = philox4x32_10(make_uint4(it, (uint32_t)a, (uint32_t)step, inst),
+                                                  A.key0, A.key1);
                     bool unv[V];
                     bool lane_any = false;
 #pragma unroll
@@ -366,6 +379,11 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                             qant[qi] = al;
                             qc[qi] = c;
                             pedge[al] = 0x80000000u | (uint32_t)qi;
+                        }
+                        // the cluster scans row c after the barrier: stage it in L2
+                        for (int j = gl * 32; j < n; j += TPA * 32) {
+                            if constexpr (!SPM) prefetch_l2(tau + (size_t)c * n + j);
+                            if (hw) prefetch_l2(hw + (size_t)c * n + j);
                         }
                         continue;
                     }
@@ -391,8 +409,6 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
 #pragma unroll
                     for (int i = 0; i < V; ++i) v[i] = unv[i] ? __fmul_rn(tv[i], wv[i]) : 0.0f;
 
-                    const uint4 x = philox4x32_10(make_uint4(it, (uint32_t)a, (uint32_t)step, inst),
-                                                  A.key0, A.key1);
                     const float q = unit24(x.x);
                     int kpick;
                     if (q < A.q0) {
@@ -498,13 +514,16 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
             cluster.sync();   // the step's edges and queues are visible cluster-wide
 
             // Phase B: the cluster's queued ants, argmax over all unvisited nodes
-            if (tid == 0) {
-                int acc = 0;
-                misc->qoff[0] = 0;
-                for (int r = 0; r < C; ++r) {
-                    acc += cluster.map_shared_rank(&misc->qn[step & 1], r)[0];
-                    misc->qoff[r + 1] = acc;
+            if (tid < 32) {
+                // lane r reads CTA r's queue length; inclusive warp scan
+                int cnt = tid < C ? cluster.map_shared_rank(&misc->qn[step & 1], tid)[0] : 0;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int o = __shfl_up_sync(0xffffffffu, cnt, off);
+                    if (tid >= off) cnt += o;
                 }
+                if (tid == 0) misc->qoff[0] = 0;
+                if (tid < C) misc->qoff[tid + 1] = cnt;
             }
             __syncthreads();
             const int Q = misc->qoff[C];
@@ -519,15 +538,18 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     eqal[tid] = cluster.map_shared_rank(qant, r)[qi];
                     const int c = cluster.map_shared_rank(qc, r)[qi];
                     eqc[tid] = c;
-                    if constexpr (SPM) {
-                        const Rec R = rec(c);
-                        for (int q2 = 0; q2 < s_slots; ++q2) {
-                            fri[tid * s_slots + q2] = ld_i<RG>(R.idx + q2);
-                            frv[tid * s_slots + q2] = ld_f<RG>(R.val + q2);
-                        }
-                    }
                 }
                 __syncthreads();
+                if constexpr (SPM) {
+                    // stage the queued ants' records, one thread per (entry, slot)
+                    for (int k = tid; k < Q * s_slots; k += nthr) {
+                        const int e = k / s_slots, q2 = k - e * s_slots;
+                        const Rec R = rec(eqc[e]);
+                        fri[k] = ld_i<RG>(R.idx + q2);
+                        frv[k] = ld_f<RG>(R.val + q2);
+                    }
+                    __syncthreads();
+                }
                 const int span = (n + C - 1) / C;
                 const int jlo = rank * span, jhi = min(n, jlo + span);
                 // warps are split among the entries so that all entries are
@@ -566,9 +588,10 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     if (Q <= nwarps) break;
                 }
                 cluster.sync();   // every CTA's partial argmax is final
-                // owners finish their queued ants
+                // owners finish their queued ants (folded into the edge gather
+                // when the step's edges are updated)
                 const int E = misc->qoff[rank + 1] - misc->qoff[rank];
-                for (int qi = tid; qi < E; qi += nthr) {
+                for (int qi = tid; qi < E && !upd; qi += nthr) {
                     const int al = qant[qi], c = qc[qi];
                     const unsigned long long key = cluster_max_entry(cluster, qpart, misc->qoff[rank] + qi, C);
                     const int next = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
@@ -598,6 +621,17 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                         const unsigned long long key = cluster_max_entry(cluster, qpart, misc->qoff[r] + qi, C);
                         u = cluster.map_shared_rank(qc, r)[qi];
                         v = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+                        if (key == 0ull || v < 0 || v >= n) {
+                            atomicExch(A.status, 4);
+                            v = u;
+                        } else if (r == rank) {
+                            // this CTA's own queued ant: finish its step
+                            const int al = a - a0;
+                            s_nxt[al] = v;
+                            if constexpr (!SPM) s_tsel[al] = __ldcg(tau + (size_t)u * n + v);
+                            tours[(size_t)a * n + step] = v;
+                            vis_base[(size_t)al * W + (v >> 5)] |= 1u << (v & 31);
+                        }
                     } else {
                         u = (int)(e >> 16);
                         v = (int)(e & 0xffffu);
@@ -610,14 +644,15 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                 // This CTA only needs the edges it writes: on the matrix its own
                 // ants' edges, on the SPM the edges that touch one of its records
                 // (their events are the only ones replayed here).
-                if (tid < m) {
-                    const int a = tid;
-                    const bool rel = SPM ? ((gu[a] % C) == rank || (gv[a] % C) == rank)
-                                         : (a >= a0 && a < a0 + ml);
-                    if (rel) eqal[atomicAdd(&misc->nrel, 1)] = a;   // eqal is free again here
+                if constexpr (SPM) {
+                    if (tid < m) {
+                        const int a = tid;
+                        if ((gu[a] % C) == rank || (gv[a] % C) == rank)
+                            eqal[atomicAdd(&misc->nrel, 1)] = a;   // eqal is free again here
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
-                const int NR = misc->nrel;
+                const int NR = SPM ? misc->nrel : ml;
                 // k = ants on the same undirected edge, representative = lowest
                 // ant; T threads per relevant edge compare it with every T-th edge
                 // (whole warps take part so that the segmented shuffles are valid)
@@ -627,7 +662,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                 if (tid < tm) {
                     const int i = tid / T, part = tid - i * T;
                     const bool valid = i < NR;
-                    const int a = valid ? eqal[i] : 0;
+                    const int a = !valid ? 0 : (SPM ? eqal[i] : a0 + i);
                     const uint32_t key = gkey[a];
                     int cnt = 0, rep = a;
                     if (valid) {
