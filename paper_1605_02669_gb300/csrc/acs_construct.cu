@@ -566,22 +566,36 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     const float* hrow = hw ? hw + (size_t)c * n : nullptr;
                     const int2 pc = xy[c];
                     unsigned long long key = 0ull;
-#pragma unroll 2
-                    for (int j = jlo + wi * 32 + lane; j < jhi; j += wpe * 32) {
-                        // the loads are issued before the visited test
-                        const uint32_t word = vis[j >> 5];
-                        float t;
-                        if constexpr (SPM) {
-                            t = tau0;
-                            for (int q2 = 0; q2 < s_slots; ++q2)
-                                if (fri[e * s_slots + q2] == j) t = frv[e * s_slots + q2];
-                        } else {
-                            t = __ldcg(trow + j);
+                    const int stride = wpe * 32;
+                    // batches of four: every load of a batch is issued before the
+                    // first is used
+                    for (int j0 = jlo + wi * 32 + lane; j0 < jhi; j0 += 4 * stride) {
+                        uint32_t word[4];
+                        float t[4], h[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int j = j0 + i * stride;
+                            word[i] = 0xffffffffu;
+                            t[i] = tau0;
+                            h[i] = 0.0f;
+                            if (j < jhi) {
+                                word[i] = vis[j >> 5];
+                                if constexpr (!SPM) t[i] = __ldcg(trow + j);
+                                h[i] = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
+                            }
                         }
-                        const float h = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
-                        if ((word >> (j & 31)) & 1u) continue;
-                        const unsigned long long k2 = pack_pj(__fmul_rn(t, h), j);
-                        key = k2 > key ? k2 : key;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int j = j0 + i * stride;
+                            if (j >= jhi || ((word[i] >> (j & 31)) & 1u)) continue;
+                            float tt = t[i];
+                            if constexpr (SPM) {
+                                for (int q2 = 0; q2 < s_slots; ++q2)
+                                    if (fri[e * s_slots + q2] == j) tt = frv[e * s_slots + q2];
+                            }
+                            const unsigned long long k2 = pack_pj(__fmul_rn(tt, h[i]), j);
+                            key = k2 > key ? k2 : key;
+                        }
                     }
                     key = warp_max_u64(key);
                     if (lane == 0 && key != 0ull) atomicMax(&qpart[e], key);
