@@ -291,7 +291,9 @@ cudaError_t configure(acs_ctx* c, int tpa, int csize)
             words += (size_t)m * c->desc_h[b].W;
         }
         ACS_TRY(dalloc(c, &c->d_vis, words));
-        ACS_TRY(cudaMemcpy(c->d_desc, c->desc_h.data(), sizeof(InstDesc) * c->B, cudaMemcpyHostToDevice));
+        ACS_TRY(cudaMemcpyAsync(c->d_desc, c->desc_h.data(), sizeof(InstDesc) * c->B,
+                                cudaMemcpyHostToDevice, c->stream));
+        ACS_TRY(cudaStreamSynchronize(c->stream));
     }
     int block = std::max(mc * tpa, m);
     block = std::min(1024, std::max(64, block));
@@ -671,13 +673,17 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
     }
     acs_status st = ACS_OK;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    // All copies go on the context's stream, in order with the trials: a
+    // device-to-device cudaMemcpy returns before the copy is done and runs on
+    // the legacy stream, which does not order against this one.
     for (Buf& x : bufs) {
         if (cudaMalloc(&x.save, x.bytes) != cudaSuccess) { cudaGetLastError(); st = ACS_ENOMEM; break; }
-        if (cudaMemcpy(x.save, x.p, x.bytes, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+        if (cudaMemcpyAsync(x.save, x.p, x.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
             st = fail_cuda(c, cudaErrorUnknown);
             break;
         }
     }
+    if (st == ACS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail_cuda(c, cudaErrorUnknown);
     const int64_t iter0 = c->iteration;
     int best_tpa = c->tpa, best_cs = c->csize;
     float best_ms = 0.0f;
@@ -701,8 +707,10 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
             cudaEventElapsedTime(&ms, e0, e1);
             if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best_tpa = tpas[ti]; best_cs = css[ci]; }
             for (Buf& x : bufs)
-                if (cudaMemcpy(x.p, x.save, x.bytes, cudaMemcpyDeviceToDevice) != cudaSuccess)
+                if (cudaMemcpyAsync(x.p, x.save, x.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
                     st = fail_cuda(c, cudaErrorUnknown);
+            if (st == ACS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
+                st = fail_cuda(c, cudaErrorUnknown);
             c->iteration = iter0;
         }
     }

@@ -239,6 +239,24 @@ def test_autotune_keeps_state(oracle_mod):
     assert_same_state(gpu, ref, 0)
 
 
+def test_autotune_on_fresh_batch_then_parity(oracle_mod):
+    # the autotuner snapshots and restores the full state between trials; on
+    # a fresh context the best tour is still uninitialised, so a restore that
+    # raced with the next trial would feed garbage nodes to the kernel
+    sizes = [120, 300, 77, 260]
+    xy, off = instances.batch(sizes, ["uniform", "clustered"] * 2, seed=9)
+    p = acs.params(m=32, cl=16, seed=12)
+    gpu = acs.Colony(xy, p, offsets=off)
+    tpa, cs = gpu.autotune(2)
+    assert gpu.iteration == 0
+    refs = [oracle.Colony(xy[off[b]:off[b + 1]], oracle.make_params(m=32, cl=16, seed=12),
+                          instance=b) for b in range(len(sizes))]
+    gpu.run(2)
+    for b, r in enumerate(refs):
+        r.run(2)
+        assert_same_state(gpu, r, 0, b)
+
+
 def test_repeatable_bits(oracle_mod):
     xy = instances.clustered(400, seed=6)
     runs = []

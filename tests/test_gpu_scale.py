@@ -1,0 +1,108 @@
+"""Full-shape runs of the batched and the large-scale workloads on the GPU.
+
+Outputs the oracle can reproduce in seconds are compared bit for bit on
+sampled instances; the rest is checked through properties that hold at any
+size: every tour is a permutation, lengths equal the recomputed EUC_2D sums,
+the best-so-far is the minimum seen, and tau0 <= tau <= 1/L_best.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_02669_gb300 import acs, instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def _lengths(xy, tours):
+    p = xy.astype(np.int64)
+    a = p[tours]
+    b = p[np.roll(tours, -1, axis=1)]
+    d2 = ((a - b) ** 2).sum(-1)
+    d = np.floor(np.sqrt(d2.astype(np.float64)) + 0.5).astype(np.int64)
+    return d.sum(1)
+
+
+def _check_properties(xy, tours, lens, best, best_len):
+    n = xy.shape[0]
+    assert (np.sort(tours, axis=1) == np.arange(n)).all()
+    assert np.array_equal(_lengths(xy, tours), lens)
+    assert best_len <= lens.min()
+    assert np.array_equal(np.sort(best), np.arange(n))
+    assert _lengths(xy, best[None, :])[0] == best_len
+
+
+def _assert_same(gpu, ref, memory, b):
+    tg, lg = gpu.tours(b)
+    tr, lr = ref.tours()
+    assert np.array_equal(tg, tr) and np.array_equal(lg, lr)
+    assert gpu.best(b)[1] == ref.best()[1]
+    if memory == 0:
+        assert np.array_equal(gpu.pheromone(b).view(np.uint32), ref.pheromone().view(np.uint32))
+    else:
+        gv, gi, gt = gpu.pheromone(b)
+        rv, ri, rt = ref.pheromone()
+        assert np.array_equal(gi, ri) and np.array_equal(gt, rt)
+        assert np.array_equal(gv.view(np.uint32), rv.view(np.uint32))
+
+
+def test_batched_256_instances(oracle_mod):
+    # 256 instances, n uniform in [100, 2500], even b uniform / odd b clustered,
+    # m=64, 32-NN, one launch per iteration for the whole batch
+    xy, off, sizes, kinds = instances.mixed_batch(256, 100, 2500, seed=3)
+    p = acs.params(m=64, cl=32, q0=0.9, seed=7)
+    gpu = acs.Colony(xy, p, offsets=off)
+    gpu.run(2)
+    for b in range(256):
+        t, L = gpu.tours(b)
+        bt, bl = gpu.best(b)
+        _check_properties(xy[off[b]:off[b + 1]], t, L, bt, bl)
+    # bit-exact against the oracle on the smallest, a middle and the largest instance
+    order = np.argsort(sizes)
+    for b in (int(order[0]), int(order[128]), int(order[-1])):
+        ref = oracle.Colony(xy[off[b]:off[b + 1]], oracle.make_params(m=64, cl=32, q0=0.9, seed=7),
+                            instance=b)
+        ref.run(2)
+        _assert_same(gpu, ref, 0, b)
+
+
+@pytest.mark.parametrize("memory", [0, 1])
+def test_large_n10000_m256_one_iteration(oracle_mod, memory):
+    xy = instances.uniform(10000, side=100000, seed=5)
+    p = acs.params(m=256, cl=32, memory=memory, spm_slots=8, seed=3)
+    gpu = acs.Colony(xy, p)
+    ref = oracle.Colony(xy, oracle.make_params(m=256, cl=32, memory=memory, spm_slots=8, seed=3))
+    gpu.run(1)
+    ref.run(1)
+    _assert_same(gpu, ref, memory, 0)
+
+
+def test_large_n20000_batch_properties(oracle_mod):
+    # two n=20000 instances on the matrix (1.6 GB each) and on the SPM
+    xy0 = instances.uniform(20000, side=100000, seed=6)
+    xy1 = instances.uniform(20000, side=100000, seed=7)
+    xy = np.concatenate([xy0, xy1])
+    off = np.array([0, 20000, 40000], np.int64)
+    for memory in (0, 1):
+        gpu = acs.Colony(xy, acs.params(m=256, cl=32, memory=memory, spm_slots=8, seed=4),
+                         offsets=off)
+        gpu.run(2)
+        for b in range(2):
+            t, L = gpu.tours(b)
+            bt, bl = gpu.best(b)
+            _check_properties(xy[off[b]:off[b + 1]], t, L, bt, bl)
+        if memory == 0:
+            tau = gpu.pheromone(0)
+            _, bl = gpu.best(0)
+            nn, w, tau0, _ = gpu.setup(0)
+            np.fill_diagonal(tau, tau0)
+            assert tau.min() >= tau0
+            assert tau.max() <= np.float32(1.0 / bl) * (1 + 2.0 ** -22)
+        gpu.close()
