@@ -87,6 +87,17 @@ def load():
     L.acs_set_cluster_size.argtypes = [_vp, _i32]
     L.acs_cluster_size.argtypes = [_vp]
     L.acs_cluster_size.restype = _i32
+    L.acs_prior_features.argtypes = [_vp, _i32, _vp, _vp]
+    L.acs_prior_count_best_edges.argtypes = [_vp, _i32, _vp, _vp]
+    L.acs_mlp_forward.argtypes = [_vp, _vp, _i64, _vp, _vp]
+    L.acs_mlp_train_batch.argtypes = [_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp, _vp]
+    _f = ctypes.c_float
+    L.acs_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _i32, _f, _f, _f, _f, _vp]
+    L.acs_apply_prior.argtypes = [_vp, _i32, _vp, _i32, _vp]
+    L.acs_set_candidates.argtypes = [_vp, _i32, _vp, _vp, _i32]
+    for name in ["acs_prior_features", "acs_prior_count_best_edges", "acs_mlp_forward",
+                 "acs_mlp_train_batch", "acs_mlp_adam", "acs_apply_prior", "acs_set_candidates"]:
+        getattr(L, name).restype = ctypes.c_int
     for name in ["acs_set_threads_per_ant", "acs_autotune", "acs_set_cluster_size", "acs_iterate_noalloc", "acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
                  "acs_best_tour", "acs_get_tours", "acs_get_pheromone", "acs_get_setup",
                  "acs_get_stats"]:
@@ -231,6 +242,65 @@ def acs_iterate_noalloc(dev_coords, n, dev_nn32, dev_w32, cl, tau0, dev_tau, dev
                                           int(cl), float(tau0), _vp(dev_tau), _vp(dev_tours),
                                           _vp(dev_lens), _vp(dev_best), _vp(dev_best_len),
                                           int(iteration), ctypes.byref(p), _vp(stream or 0)))
+
+
+# ---- learned prior (include/acs_prior.h); device buffers are torch tensors or raw
+# device addresses, streams torch streams, raw handles or None (legacy default)
+
+ACS_MLP_FEATURES, ACS_MLP_HIDDEN, ACS_MLP_PARAMS = 8, 64, 4801
+
+
+def _dev(t):
+    if t is None:
+        return None
+    return _vp(t if isinstance(t, int) else t.data_ptr())
+
+
+def _strm(s):
+    if s is None:
+        return None
+    return _vp(s if isinstance(s, int) else s.cuda_stream)
+
+
+def acs_prior_features(ctx, instance, dev_feat, stream=None):
+    _check(load().acs_prior_features(ctx, instance, _dev(dev_feat), _strm(stream)),
+           "acs_prior_features")
+
+
+def acs_prior_count_best_edges(ctx, instance, dev_count, stream=None):
+    _check(load().acs_prior_count_best_edges(ctx, instance, _dev(dev_count), _strm(stream)),
+           "acs_prior_count_best_edges")
+
+
+def acs_mlp_forward(dev_params, dev_feat, rows, dev_p, stream=None):
+    _check(load().acs_mlp_forward(_dev(dev_params), _dev(dev_feat), rows, _dev(dev_p),
+                                  _strm(stream)), "acs_mlp_forward")
+
+
+def acs_mlp_train_batch(dev_params, dev_feat, dev_label, total, first, batch, perm_a, perm_c,
+                        dev_grad, dev_loss, stream=None):
+    _check(load().acs_mlp_train_batch(_dev(dev_params), _dev(dev_feat), _dev(dev_label), total,
+                                      first, batch, perm_a, perm_c, _dev(dev_grad),
+                                      _dev(dev_loss), _strm(stream)), "acs_mlp_train_batch")
+
+
+def acs_mlp_adam(dev_params, dev_grad, dev_m, dev_v, step, lr=1e-3, beta1=0.9, beta2=0.999,
+                 eps=1e-8, stream=None):
+    _check(load().acs_mlp_adam(_dev(dev_params), _dev(dev_grad), _dev(dev_m), _dev(dev_v), step,
+                               lr, beta1, beta2, eps, _strm(stream)), "acs_mlp_adam")
+
+
+def acs_apply_prior(ctx, instance, dev_p, keep, stream=None):
+    _check(load().acs_apply_prior(ctx, instance, _dev(dev_p), keep, _strm(stream)),
+           "acs_apply_prior")
+
+
+def acs_set_candidates(ctx, instance, nn, w):
+    nn = np.ascontiguousarray(nn, np.int32)
+    w = np.ascontiguousarray(w, np.float32)
+    assert nn.shape == w.shape and nn.ndim == 2
+    _check(load().acs_set_candidates(ctx, instance, _ptr(nn), _ptr(w), nn.shape[1]),
+           "acs_set_candidates")
 
 
 def acs_destroy(ctx):

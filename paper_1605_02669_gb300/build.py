@@ -8,7 +8,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libacs.so")
-SOURCES = ["acs_api.cu", "acs_construct.cu", "acs_noalloc.cu"]
+SOURCES = ["acs_api.cu", "acs_construct.cu", "acs_noalloc.cu", "acs_prior.cu"]
 HEADERS = ["acs_internal.cuh", "acs_device.cuh"]
 
 NVCC_FLAGS = [
@@ -32,6 +32,7 @@ def _stale():
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     deps.append(os.path.join(ROOT, "include", "acs.h"))
+    deps.append(os.path.join(ROOT, "include", "acs_prior.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 

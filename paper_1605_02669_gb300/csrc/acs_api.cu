@@ -518,6 +518,42 @@ acs_status check_device_status(acs_ctx* c)
 
 }  // namespace
 
+// ------------------------------------------------------------------ for acs_prior.cu
+
+namespace acs {
+
+acs_status ctx_view(acs_ctx* c, int b, CtxView* v)
+{
+    if (!c || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    const InstDesc& D = c->desc_h[b];
+    v->n = D.n;
+    v->cl = D.cl;
+    v->xy = c->d_xy + 2 * D.xy_off;
+    v->nn = c->d_nn + 32 * D.row_off;
+    v->w = c->d_w + 32 * D.row_off;
+    v->best = c->d_best + D.node_off;
+    v->stream = c->stream;
+    v->has_best = c->iteration > 0;
+    return check_device_status(c);
+}
+
+// New effective candidate width of instance b (rows already rewritten on the
+// context's stream). The descriptor copy is ordered on the same stream.
+cudaError_t ctx_set_cl(acs_ctx* c, int b, int cl)
+{
+    c->desc_h[b].cl = cl;
+    c->cl[b] = cl;
+    cudaError_t e = cudaMemcpyAsync(c->d_desc + b, &c->desc_h[b], sizeof(InstDesc),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e;
+}
+
+void ctx_poison(acs_ctx* c) { c->poisoned = true; }
+
+}  // namespace acs
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {

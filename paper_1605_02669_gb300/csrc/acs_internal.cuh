@@ -109,4 +109,15 @@ __host__ __device__ inline SmemLayout smem_layout(int m, int mc, int nrec, int s
     return L;
 }
 
+// What the learned-prior entry points need from a context (acs_api.cu).
+struct CtxView {
+    int n, cl;
+    const int32_t* xy;   // coordinates of the instance [n][2]
+    int32_t* nn;         // candidate rows [n][32]
+    float* w;            // candidate weights [n][32]
+    const int32_t* best; // best-so-far tour [n]
+    void* stream;        // cudaStream_t of the context
+    bool has_best;
+};
+
 }  // namespace acs

@@ -1,0 +1,665 @@
+// acs_prior.cu -- the learned edge prior: features, labels, the BF16
+// tensor-core MLP (forward, fused forward+backward, Adam) and the pruning /
+// reweighting of the candidate rows. See include/acs_prior.h.
+//
+// Tensor-core layout. A warp handles 16 feature rows (edges) at a time with
+// mma.sync m16n8k16 (BF16 operands, FP32 accumulators):
+//   layer 1: [16 x 16] x [16 x 64]   (8 features zero-padded to K = 16)
+//   layer 2: [16 x 64] x [64 x 64]
+//   layer 3: a dot product with w3 in FP32 on the CUDA cores (N = 1).
+// The FP32 accumulator fragment of one layer is, element for element, the
+// BF16 A fragment of the next layer, so activations never leave registers.
+// The backward pass recomputes the forward, forms dh2 and dh1 the same way,
+// and accumulates the weight gradients dW2 = h1^T dh2 and dW1 = x^T dh1 as
+// GEMMs over the 128 edges of a CTA block, reading the transposed operands
+// from shared memory with ldmatrix.trans.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <new>
+
+#include "acs.h"
+#include "acs_device.cuh"
+#include "acs_internal.cuh"
+#include "acs_prior.h"
+
+namespace acs {
+acs_status ctx_view(acs_ctx* c, int b, CtxView* v);
+cudaError_t ctx_set_cl(acs_ctx* c, int b, int cl);
+void ctx_poison(acs_ctx* c);
+}  // namespace acs
+
+using namespace acs;
+
+namespace {
+
+constexpr int kW1 = 0, kB1 = 512, kW2 = 576, kB2 = 4672, kW3 = 4736, kB3 = 4800;
+constexpr int kPadK1 = 24;   // smem row of W1^T: 16 K values + 8 pad (bank spread)
+constexpr int kPad64 = 72;   // smem row of a 64-wide BF16 tile: 64 + 8 pad
+constexpr int kBlockRows = 128;  // rows of a training block (8 warps x 16)
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const void* p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// Weights as BF16 in shared memory, biases in FP32.
+struct MlpSmem {
+    uint16_t w1t[64][kPadK1];   // w1t[h][f] = W1[f][h], f >= 8 zero
+    uint16_t w2t[64][kPad64];   // w2t[out][in] = W2[in][out]  (forward B operand)
+    uint16_t w2[64][kPad64];    // w2[in][out]                  (backward B operand)
+    float w3[64];
+    float b1[64], b2[64], b3;
+};
+
+constexpr size_t round16(size_t x) { return (x + 15) & ~size_t(15); }
+// dynamic shared memory of the training kernel: weights, then the block's
+// x, h1, dh2 and dh1 tiles (16-byte aligned rows for ldmatrix), then the
+// bias / w3 gradient partials
+constexpr size_t kOffX = round16(sizeof(MlpSmem));
+constexpr size_t kOffH1 = kOffX + sizeof(uint16_t) * kBlockRows * kPadK1;
+constexpr size_t kOffRed = kOffH1 + 3 * sizeof(uint16_t) * kBlockRows * kPad64;
+constexpr size_t kTrainSmem = kOffRed + sizeof(float) * (3 * 64 + 1);
+static_assert(kOffH1 % 16 == 0 && kOffRed % 16 == 0, "ldmatrix rows need 16-byte alignment");
+
+__device__ void load_weights(MlpSmem& S, const float* P, bool need_w2)
+{
+    for (int i = threadIdx.x; i < 64 * kPadK1; i += blockDim.x) {
+        const int h = i / kPadK1, f = i - h * kPadK1;
+        const float v = f < 8 ? P[kW1 + f * 64 + h] : 0.0f;
+        S.w1t[h][f] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int in = i >> 6, out = i & 63;
+        const uint16_t v = __bfloat16_as_ushort(__float2bfloat16_rn(P[kW2 + i]));
+        S.w2t[out][in] = v;
+        if (need_w2) S.w2[in][out] = v;
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        S.w3[i] = P[kW3 + i];
+        S.b1[i] = P[kB1 + i];
+        S.b2[i] = P[kB2 + i];
+    }
+    if (threadIdx.x == 0) S.b3 = P[kB3];
+}
+
+// Per-warp forward of 16 rows: lane (g, t) = (lane / 4, lane % 4) holds rows
+// g and g+8 of the tile (feature rows row0 and row1; absent when < 0). Leaves
+// in registers the relu masks, the h1 A fragments (BF16), h2 (FP32) and the
+// logits. Layer 3 (N = 1) runs in FP32 on the CUDA cores.
+struct Fwd {
+    uint32_t h1a[4][4];   // layer-2 A fragments (BF16 pairs), k-tile major
+    float h2[8][4];       // relu(h1 W2 + b2), C-fragment layout
+    uint32_t m1, m2;      // relu masks: bit nt*4+i of the C fragments
+    float z0, z1;         // logits of rows g and g+8
+};
+
+__device__ __forceinline__ void mlp_fwd_tile(const MlpSmem& S, const uint16_t* feat, int64_t row0,
+                                             int64_t row1, Fwd& F)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // layer-1 A fragment: rows g and g+8, features t*2, t*2+1 (K 8..15 are zero)
+    uint32_t a[4];
+    a[0] = row0 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row0 * 8 + t * 2) : 0u;
+    a[1] = row1 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row1 * 8 + t * 2) : 0u;
+    a[2] = 0u;
+    a[3] = 0u;
+    float c1[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.0f;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w1t[nt * 8 + g][t * 2]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w1t[nt * 8 + g][t * 2 + 8]);
+        mma16816(c1[nt], a, b0, b1);
+    }
+    F.m1 = 0u;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int col = nt * 8 + t * 2;
+        float v[4];
+        v[0] = c1[nt][0] + S.b1[col];
+        v[1] = c1[nt][1] + S.b1[col + 1];
+        v[2] = c1[nt][2] + S.b1[col];
+        v[3] = c1[nt][3] + S.b1[col + 1];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (v[i] > 0.0f) F.m1 |= 1u << (nt * 4 + i);
+            else v[i] = 0.0f;
+        }
+        // C fragment (rows g/g+8, cols col/col+1) -> A fragment of k-tile nt/2
+        const int kt = nt >> 1, hi = nt & 1;
+        F.h1a[kt][0 + 2 * hi] = pack_bf16(v[0], v[1]);
+        F.h1a[kt][1 + 2 * hi] = pack_bf16(v[2], v[3]);
+    }
+    float c2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        c2[nt][0] = c2[nt][1] = c2[nt][2] = c2[nt][3] = 0.0f;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w2t[nt * 8 + g][kt * 16 + t * 2]);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w2t[nt * 8 + g][kt * 16 + 8 + t * 2]);
+            mma16816(c2[nt], F.h1a[kt], b0, b1);
+        }
+    }
+    F.m2 = 0u;
+    float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int col = nt * 8 + t * 2;
+        float v[4];
+        v[0] = c2[nt][0] + S.b2[col];
+        v[1] = c2[nt][1] + S.b2[col + 1];
+        v[2] = c2[nt][2] + S.b2[col];
+        v[3] = c2[nt][3] + S.b2[col + 1];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (v[i] > 0.0f) F.m2 |= 1u << (nt * 4 + i);
+            F.h2[nt][i] = v[i] > 0.0f ? v[i] : 0.0f;
+        }
+        const float wa = S.w3[col], wb = S.w3[col + 1];
+        z0 += F.h2[nt][0] * wa + F.h2[nt][1] * wb;
+        z1 += F.h2[nt][2] * wa + F.h2[nt][3] * wb;
+    }
+    // the four lanes of a quad hold the 64 columns of rows g and g+8
+    z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+    z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+    z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+    z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+    F.z0 = z0 + S.b3;
+    F.z1 = z1 + S.b3;
+}
+
+__device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// mean-BCE term of one row: max(z,0) - z y + log(1 + exp(-|z|))
+__device__ __forceinline__ float bce_term(float z, float y)
+{
+    return fmaxf(z, 0.0f) - z * y + log1pf(expf(-fabsf(z)));
+}
+
+__global__ void mlp_forward_kernel(const float* P, const uint16_t* feat, int64_t rows, float* pout)
+{
+    __shared__ MlpSmem S;
+    load_weights(S, P, false);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t tiles = (rows + 15) / 16;
+    for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tile < tiles;
+         tile += warps) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        Fwd F;
+        mlp_fwd_tile(S, feat, r0 < rows ? r0 : -1, r1 < rows ? r1 : -1, F);
+        if (t == 0) {
+            if (r0 < rows) pout[r0] = sigmoidf(F.z0);
+            if (r1 < rows) pout[r1] = sigmoidf(F.z1);
+        }
+    }
+}
+
+// Forward + backward over one mini-batch; gradients of the mean loss are
+// accumulated into grad (zeroed by the caller) and the loss into loss[0].
+__global__ void __launch_bounds__(256, 1)
+mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64_t total,
+                 int64_t first, int64_t batch, int64_t pa, int64_t pc, float* grad, float* loss)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    MlpSmem& S = *reinterpret_cast<MlpSmem*>(dsm);
+    uint16_t (*xs)[kPadK1] = reinterpret_cast<uint16_t (*)[kPadK1]>(dsm + kOffX);
+    uint16_t (*h1s)[kPad64] = reinterpret_cast<uint16_t (*)[kPad64]>(dsm + kOffH1);
+    uint16_t (*dh2s)[kPad64] = h1s + kBlockRows;
+    uint16_t (*dh1s)[kPad64] = dh2s + kBlockRows;
+    float* red = reinterpret_cast<float*>(dsm + kOffRed);   // b1, b2, w3 partials, then b3
+    load_weights(S, P, true);
+    for (int i = threadIdx.x; i < 3 * 64 + 1; i += blockDim.x) red[i] = 0.0f;
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float inv_b = 1.0f / (float)batch;
+    float acc[8][4];   // warps 0-3: dW2 rows warp*16.., warp 4: dW1 (rows = features)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+    float lsum = 0.0f;
+
+    const int64_t blocks = (batch + kBlockRows - 1) / kBlockRows;
+    for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
+        const int64_t b0 = blk * kBlockRows + warp * 16 + g, b1 = b0 + 8;
+        const int64_t row0 = b0 < batch ? (int64_t)(((unsigned __int128)pa * (unsigned __int128)(first + b0) + pc) % (unsigned __int128)total) : -1;
+        const int64_t row1 = b1 < batch ? (int64_t)(((unsigned __int128)pa * (unsigned __int128)(first + b1) + pc) % (unsigned __int128)total) : -1;
+        Fwd F;
+        mlp_fwd_tile(S, feat, row0, row1, F);
+        const int lr0 = warp * 16 + g, lr1 = lr0 + 8;   // rows of the CTA block
+        // x tile for dW1 (features 0..7, 8..15 zero)
+        *reinterpret_cast<uint32_t*>(&xs[lr0][t * 2]) =
+            row0 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row0 * 8 + t * 2) : 0u;
+        *reinterpret_cast<uint32_t*>(&xs[lr1][t * 2]) =
+            row1 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row1 * 8 + t * 2) : 0u;
+        *reinterpret_cast<uint32_t*>(&xs[lr0][t * 2 + 8]) = 0u;
+        *reinterpret_cast<uint32_t*>(&xs[lr1][t * 2 + 8]) = 0u;
+        // h1 tile for dW2
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int kt = nt >> 1, hi = nt & 1;
+            *reinterpret_cast<uint32_t*>(&h1s[lr0][nt * 8 + t * 2]) = F.h1a[kt][0 + 2 * hi];
+            *reinterpret_cast<uint32_t*>(&h1s[lr1][nt * 8 + t * 2]) = F.h1a[kt][1 + 2 * hi];
+        }
+        // dL/dz of the mean loss, and the loss itself
+        float dz0 = 0.0f, dz1 = 0.0f;
+        if (row0 >= 0) {
+            const float y = label[row0];
+            dz0 = (sigmoidf(F.z0) - y) * inv_b;
+            if (t == 0) lsum += bce_term(F.z0, y);
+        }
+        if (row1 >= 0) {
+            const float y = label[row1];
+            dz1 = (sigmoidf(F.z1) - y) * inv_b;
+            if (t == 0) lsum += bce_term(F.z1, y);
+        }
+        // dw3, db3, dh2 = dz w3 * relu'(a2), db2
+        uint32_t dh2a[4][4];
+        float pw3[16], pb2[16];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = nt * 8 + t * 2;
+            const float wa = S.w3[col], wb = S.w3[col + 1];
+            pw3[nt * 2] = F.h2[nt][0] * dz0 + F.h2[nt][2] * dz1;
+            pw3[nt * 2 + 1] = F.h2[nt][1] * dz0 + F.h2[nt][3] * dz1;
+            float d[4];
+            d[0] = (F.m2 >> (nt * 4 + 0)) & 1u ? dz0 * wa : 0.0f;
+            d[1] = (F.m2 >> (nt * 4 + 1)) & 1u ? dz0 * wb : 0.0f;
+            d[2] = (F.m2 >> (nt * 4 + 2)) & 1u ? dz1 * wa : 0.0f;
+            d[3] = (F.m2 >> (nt * 4 + 3)) & 1u ? dz1 * wb : 0.0f;
+            pb2[nt * 2] = d[0] + d[2];
+            pb2[nt * 2 + 1] = d[1] + d[3];
+            const int kt = nt >> 1, hi = nt & 1;
+            dh2a[kt][0 + 2 * hi] = pack_bf16(d[0], d[1]);
+            dh2a[kt][1 + 2 * hi] = pack_bf16(d[2], d[3]);
+            *reinterpret_cast<uint32_t*>(&dh2s[lr0][col]) = dh2a[kt][0 + 2 * hi];
+            *reinterpret_cast<uint32_t*>(&dh2s[lr1][col]) = dh2a[kt][1 + 2 * hi];
+        }
+        // dh1 = dh2 W2^T * relu'(a1)   (B(k=out, n=in) = W2[in][out] = w2[n][k])
+        float pb1[16];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                const uint32_t bb0 = *reinterpret_cast<const uint32_t*>(&S.w2[nt * 8 + g][kt * 16 + t * 2]);
+                const uint32_t bb1 = *reinterpret_cast<const uint32_t*>(&S.w2[nt * 8 + g][kt * 16 + 8 + t * 2]);
+                mma16816(c, dh2a[kt], bb0, bb1);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (!((F.m1 >> (nt * 4 + i)) & 1u)) c[i] = 0.0f;
+            pb1[nt * 2] = c[0] + c[2];
+            pb1[nt * 2 + 1] = c[1] + c[3];
+            const int col = nt * 8 + t * 2;
+            *reinterpret_cast<uint32_t*>(&dh1s[lr0][col]) = pack_bf16(c[0], c[1]);
+            *reinterpret_cast<uint32_t*>(&dh1s[lr1][col]) = pack_bf16(c[2], c[3]);
+        }
+        // column sums over the 8 row groups of the warp, then into shared memory
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+#pragma unroll
+            for (int off = 4; off < 32; off <<= 1) {
+                pw3[i] += __shfl_xor_sync(0xffffffffu, pw3[i], off);
+                pb2[i] += __shfl_xor_sync(0xffffffffu, pb2[i], off);
+                pb1[i] += __shfl_xor_sync(0xffffffffu, pb1[i], off);
+            }
+        }
+        if (g == 0) {
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = nt * 8 + t * 2;
+                atomicAdd(&red[col], pb1[nt * 2]);
+                atomicAdd(&red[col + 1], pb1[nt * 2 + 1]);
+                atomicAdd(&red[64 + col], pb2[nt * 2]);
+                atomicAdd(&red[64 + col + 1], pb2[nt * 2 + 1]);
+                atomicAdd(&red[128 + col], pw3[nt * 2]);
+                atomicAdd(&red[128 + col + 1], pw3[nt * 2 + 1]);
+            }
+        }
+        float dzs = dz0 + dz1;
+#pragma unroll
+        for (int off = 4; off < 32; off <<= 1) dzs += __shfl_xor_sync(0xffffffffu, dzs, off);
+        if (lane == 0) atomicAdd(&red[192], dzs);
+        __syncthreads();
+        // weight gradients over the block's 128 rows (K = rows):
+        //   warps 0-3: dW2[in = warp*16 ..][out] = sum_r h1[r][in] dh2[r][out]
+        //   warp 4:    dW1[f][in]              = sum_r x[r][f]  dh1[r][in]
+        if (warp < 5) {
+            uint16_t (*As)[kPad64] = h1s;
+            uint16_t (*Bs)[kPad64] = warp < 4 ? dh2s : dh1s;
+            const int m0 = warp < 4 ? warp * 16 : 0;
+            const int q = lane >> 3, r8 = lane & 7;
+#pragma unroll 1
+            for (int k0 = 0; k0 < kBlockRows; k0 += 16) {
+                uint32_t af[4];
+                const int arow = k0 + r8 + ((q & 2) ? 8 : 0), acol = m0 + ((q & 1) ? 8 : 0);
+                if (warp < 4) ldsm_x4_trans(af, &As[arow][acol]);
+                else ldsm_x4_trans(af, &xs[arow][acol]);
+#pragma unroll
+                for (int np = 0; np < 4; ++np) {
+                    uint32_t bf[4];
+                    const int brow = k0 + r8 + ((q & 1) ? 8 : 0), bcol = np * 16 + ((q & 2) ? 8 : 0);
+                    ldsm_x4_trans(bf, &Bs[brow][bcol]);
+                    mma16816(acc[np * 2], af, bf[0], bf[1]);
+                    mma16816(acc[np * 2 + 1], af, bf[2], bf[3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // flush the CTA's partial gradients
+    if (warp < 4) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int in0 = warp * 16 + g, out = nt * 8 + t * 2;
+            atomicAdd(&grad[kW2 + in0 * 64 + out], acc[nt][0]);
+            atomicAdd(&grad[kW2 + in0 * 64 + out + 1], acc[nt][1]);
+            atomicAdd(&grad[kW2 + (in0 + 8) * 64 + out], acc[nt][2]);
+            atomicAdd(&grad[kW2 + (in0 + 8) * 64 + out + 1], acc[nt][3]);
+        }
+    } else if (warp == 4) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int out = nt * 8 + t * 2;   // rows g < 8 are the real features
+            atomicAdd(&grad[kW1 + g * 64 + out], acc[nt][0]);
+            atomicAdd(&grad[kW1 + g * 64 + out + 1], acc[nt][1]);
+        }
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        atomicAdd(&grad[kB1 + i], red[i]);
+        atomicAdd(&grad[kB2 + i], red[64 + i]);
+        atomicAdd(&grad[kW3 + i], red[128 + i]);
+    }
+    if (threadIdx.x == 0) atomicAdd(&grad[kB3], red[192]);
+    float l = lsum;   // non-zero on lanes t == 0 only
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if (lane == 0) atomicAdd(loss, l * inv_b);
+}
+
+__global__ void adam_kernel(float* P, const float* G, float* M, float* Vv, int n, float lr, float b1,
+                            float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float m = b1 * M[i] + (1.0f - b1) * g;
+    const float v = b2 * Vv[i] + (1.0f - b2) * g * g;
+    M[i] = m;
+    Vv[i] = v;
+    P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// Per-node statistics of the candidate graph: mean and last candidate
+// distance (each at least 1), in-degree.
+__global__ void node_stats_kernel(const int32_t* xy, const int32_t* nn, int n, int cl, float* dmean,
+                                  float* dlast, int* indeg)
+{
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int2* p = reinterpret_cast<const int2*>(xy);
+    int d = 0;
+    if (lane < cl) {
+        const int j = nn[(size_t)i * 32 + lane];
+        d = euc2d(p[i], p[j]);
+        atomicAdd(&indeg[j], 1);
+    }
+    int s = d;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const int dl = __shfl_sync(0xffffffffu, d, cl - 1);
+    if (lane == 0) {
+        dmean[i] = fmaxf((float)s / (float)cl, 1.0f);
+        dlast[i] = (float)max(dl, 1);
+    }
+}
+
+__global__ void features_kernel(const int32_t* xy, const int32_t* nn, int n, int cl, const float* dmean,
+                                const float* dlast, const int* indeg, uint16_t* feat)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * 32) return;
+    const int i = (int)(e >> 5), k = (int)(e & 31);
+    float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < cl) {
+        const int2* p = reinterpret_cast<const int2*>(xy);
+        const int j = nn[e];
+        const float d = (float)euc2d(p[i], p[j]);
+        const float fcl = (float)cl;
+        f[0] = (float)k / fcl;
+        f[1] = d / dmean[i];
+        f[2] = d / dlast[i];
+        f[3] = (float)(p[j].x - p[i].x) / dlast[i];
+        f[4] = (float)(p[j].y - p[i].y) / dlast[i];
+        float rv = 1.0f;
+        for (int q = 0; q < cl; ++q)
+            if (nn[(size_t)j * 32 + q] == i) { rv = (float)q / fcl; break; }
+        f[5] = rv;
+        f[6] = d / dlast[j];
+        f[7] = (float)indeg[j] / fcl;
+    }
+    uint4 out;
+    out.x = pack_bf16(f[0], f[1]);
+    out.y = pack_bf16(f[2], f[3]);
+    out.z = pack_bf16(f[4], f[5]);
+    out.w = pack_bf16(f[6], f[7]);
+    *reinterpret_cast<uint4*>(feat + e * 8) = out;
+}
+
+__global__ void count_best_edges_kernel(const int32_t* nn, const int32_t* best, int n, int cl, float* count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int u = best[i], v = best[i + 1 < n ? i + 1 : 0];
+    for (int side = 0; side < 2; ++side) {
+        const int a = side ? v : u, b = side ? u : v;
+        for (int k = 0; k < cl; ++k)
+            if (nn[(size_t)a * 32 + k] == b) { atomicAdd(&count[(size_t)a * 32 + k], 1.0f); break; }
+    }
+}
+
+// One warp per node: keep the `keep` best scores (ties -> lower rank) in rank
+// order, reweighted w' = w * p; pad the rest of the row.
+__global__ void apply_prior_kernel(int32_t* nn, float* w, const float* score, int n, int cl, int keep)
+{
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const size_t e = (size_t)i * 32 + lane;
+    const bool valid = lane < cl;
+    const float p = valid ? score[e] : -1.0f;
+    const int j = nn[e];
+    const float wv = w[e];
+    int rank = 0;   // candidates that beat this one
+    for (int o = 0; o < 32; ++o) {
+        const float po = __shfl_sync(0xffffffffu, p, o);
+        if (o < cl && valid && (po > p || (po == p && o < lane))) ++rank;
+    }
+    const bool kept = valid && rank < keep;
+    const unsigned bal = __ballot_sync(0xffffffffu, kept);
+    const int pos = __popc(bal & ((1u << lane) - 1u));
+    __syncwarp();
+    if (kept) {
+        nn[(size_t)i * 32 + pos] = j;
+        w[(size_t)i * 32 + pos] = __fmul_rn(wv, p);
+    }
+    __syncwarp();
+    if (lane >= keep) {
+        nn[e] = -1;
+        w[e] = 0.0f;
+    }
+}
+
+acs_status launched(cudaError_t e) { return e == cudaSuccess ? ACS_OK : ACS_ECUDA; }
+
+}  // namespace
+
+extern "C" {
+
+acs_status acs_prior_features(acs_ctx* ctx, int32_t instance, uint16_t* dev_feat, void* stream)
+{
+    CtxView v;
+    if (!dev_feat) return ACS_EINVAL;
+    if (acs_status s = ctx_view(ctx, instance, &v)) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // scratch of the candidate-graph statistics (stream-ordered allocation)
+    void* scratch = nullptr;
+    const size_t bytes = (size_t)v.n * (2 * sizeof(float) + sizeof(int));
+    if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) { cudaGetLastError(); return ACS_ENOMEM; }
+    float* dmean = static_cast<float*>(scratch);
+    float* dlast = dmean + v.n;
+    int* indeg = reinterpret_cast<int*>(dlast + v.n);
+    cudaError_t e = cudaMemsetAsync(indeg, 0, sizeof(int) * v.n, st);
+    if (e == cudaSuccess) {
+        node_stats_kernel<<<(v.n + 7) / 8, 256, 0, st>>>(v.xy, v.nn, v.n, v.cl, dmean, dlast, indeg);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int64_t rows = (int64_t)v.n * 32;
+        features_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(v.xy, v.nn, v.n, v.cl, dmean,
+                                                                       dlast, indeg, dev_feat);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(scratch, st);
+    return launched(e);
+}
+
+acs_status acs_prior_count_best_edges(acs_ctx* ctx, int32_t instance, float* dev_count, void* stream)
+{
+    CtxView v;
+    if (!dev_count) return ACS_EINVAL;
+    if (acs_status s = ctx_view(ctx, instance, &v)) return s;
+    if (!v.has_best) return ACS_ESTATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    count_best_edges_kernel<<<(v.n + 255) / 256, 256, 0, st>>>(v.nn, v.best, v.n, v.cl, dev_count);
+    return launched(cudaGetLastError());
+}
+
+acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, int64_t rows, float* dev_p,
+                           void* stream)
+{
+    if (rows == 0) return ACS_OK;
+    if (!dev_params || !dev_feat || !dev_p || rows < 0) return ACS_EINVAL;
+    const int64_t tiles = (rows + 15) / 16;
+    const int grid = (int)(tiles / 8 + 1 < 4096 ? tiles / 8 + 1 : 4096);
+    mlp_forward_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(dev_params, dev_feat, rows, dev_p);
+    return launched(cudaGetLastError());
+}
+
+acs_status acs_mlp_train_batch(const float* dev_params, const uint16_t* dev_feat, const float* dev_label,
+                               int64_t total, int64_t first, int64_t batch, int64_t perm_a, int64_t perm_c,
+                               float* dev_grad, float* dev_loss, void* stream)
+{
+    if (!dev_params || !dev_feat || !dev_label || !dev_grad || !dev_loss || total < 1 || batch < 1 ||
+        first < 0 || perm_a < 1 || perm_c < 0)
+        return ACS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(dev_grad, 0, sizeof(float) * ACS_MLP_PARAMS, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev_loss, 0, sizeof(float), st);
+    const size_t smem = kTrainSmem;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return ACS_ECUDA;
+    const int64_t blocks = (batch + kBlockRows - 1) / kBlockRows;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)(blocks < sms ? blocks : sms);
+    mlp_train_kernel<<<grid, 256, smem, st>>>(dev_params, dev_feat, dev_label, total, first, batch, perm_a,
+                                              perm_c, dev_grad, dev_loss);
+    return launched(cudaGetLastError());
+}
+
+acs_status acs_mlp_adam(float* dev_params, const float* dev_grad, float* dev_m, float* dev_v, int32_t step,
+                        float lr, float beta1, float beta2, float eps, void* stream)
+{
+    if (!dev_params || !dev_grad || !dev_m || !dev_v || step < 1) return ACS_EINVAL;
+    // bias corrections in double: 1 - beta2^t cancels heavily in FP32 for small t
+    const float c1 = (float)(1.0 - pow((double)beta1, (double)step));
+    const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
+    adam_kernel<<<(ACS_MLP_PARAMS + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        dev_params, dev_grad, dev_m, dev_v, ACS_MLP_PARAMS, lr, beta1, beta2, eps, c1, c2);
+    return launched(cudaGetLastError());
+}
+
+acs_status acs_apply_prior(acs_ctx* ctx, int32_t instance, const float* dev_p, int32_t keep, void* stream)
+{
+    CtxView v;
+    if (!dev_p) return ACS_EINVAL;
+    if (acs_status s = ctx_view(ctx, instance, &v)) return s;
+    if (keep < 1 || keep > v.cl) return ACS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    apply_prior_kernel<<<(v.n + 7) / 8, 256, 0, st>>>(v.nn, v.w, dev_p, v.n, v.cl, keep);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = ctx_set_cl(ctx, instance, keep);
+    if (e != cudaSuccess) {
+        ctx_poison(ctx);
+        return ACS_ECUDA;
+    }
+    return ACS_OK;
+}
+
+acs_status acs_set_candidates(acs_ctx* ctx, int32_t instance, const int32_t* nn, const float* w, int32_t cl)
+{
+    CtxView v;
+    if (!nn || !w) return ACS_EINVAL;
+    if (acs_status s = ctx_view(ctx, instance, &v)) return s;
+    if (cl < 1 || cl > 32 || cl > v.n - 1) return ACS_EINVAL;
+    for (int i = 0; i < v.n; ++i)
+        for (int k = 0; k < cl; ++k) {
+            const int32_t j = nn[(size_t)i * cl + k];
+            if (j < 0 || j >= v.n || j == i || !(w[(size_t)i * cl + k] >= 0.0f)) return ACS_EINVAL;
+        }
+    int32_t* rn = new (std::nothrow) int32_t[(size_t)v.n * 32];
+    float* rw = new (std::nothrow) float[(size_t)v.n * 32];
+    if (!rn || !rw) {
+        delete[] rn;
+        delete[] rw;
+        return ACS_ENOMEM;
+    }
+    for (int i = 0; i < v.n; ++i)
+        for (int k = 0; k < 32; ++k) {
+            rn[(size_t)i * 32 + k] = k < cl ? nn[(size_t)i * cl + k] : -1;
+            rw[(size_t)i * 32 + k] = k < cl ? w[(size_t)i * cl + k] : 0.0f;
+        }
+    cudaStream_t st = (cudaStream_t)v.stream;
+    cudaError_t e = cudaMemcpyAsync(v.nn, rn, sizeof(int32_t) * v.n * 32, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v.w, rw, sizeof(float) * v.n * 32, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    delete[] rn;
+    delete[] rw;
+    if (e == cudaSuccess) e = ctx_set_cl(ctx, instance, cl);
+    if (e != cudaSuccess) {
+        ctx_poison(ctx);
+        return ACS_ECUDA;
+    }
+    return ACS_OK;
+}
+
+}  // extern "C"
