@@ -10,6 +10,10 @@ four colonies; the matrix and SPM contexts run concurrently on two streams.
 Metric: ant-steps/s = sum over colonies of m*(n-1) per iteration / step time.
 L2 is flushed (256 MiB write) between timed steps, outside the timed events.
 
+Beside it, the JSON line carries the second half of the metric: the mean
+tour-length gap at equal GPU time of the learned prior against plain ACS on
+held-out n=2392 and n=5000 instances (gap_leg; --no-gap skips it).
+
 --impl reference times the CPU oracle (single thread) on a bounded sample of
 the same workload: each step is one oracle iteration of one of the four
 colonies in rotation.
@@ -137,6 +141,29 @@ def dist_setup(args):
     return rank, world, local
 
 
+def rank_seed(rank):
+    """Each rank runs its own copy of the workload: instances and Philox seed
+    offset by the rank (independent units, no collective on the data path)."""
+    return {"instances_seed_offset": rank, "philox_seed": 1 + rank}
+
+
+def max_over_ranks(x, world, device):
+    """The job's time is the slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, total_ms):
+    """Whole-job units per second: every rank processed units_per_rank."""
+    return units_per_rank * world / (total_ms / 1000.0)
+
+
 def run_reference(args, rank, world):
     """CPU oracle, single thread, bounded sample (one colony-iteration per step)."""
     import oracle
@@ -210,6 +237,32 @@ def cpu_baseline_leg(seconds_budget=15.0):
                       "m=128), single thread, %.1f s" % t_total}
 
 
+KERNEL_SOURCES = ["acs_construct.cu", "acs_device.cuh", "acs_internal.cuh"]
+# DRAM bytes (read + write) of one construct launch of this workload, from one
+# ncu capture each (profiles/), keyed by (memory, threads per ant, cluster
+# size) and valid only for the kernel sources they were taken on.
+CAPTURED_TRAFFIC = {
+    ("matrix", 32, 16): {"bytes": 36976128 + 370432, "sources": "e541c7890bd7"},
+}
+
+
+def kernel_sources_digest():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1605_02669_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def kernel_traffic(memory, tpa, csize):
+    rec = CAPTURED_TRAFFIC.get((memory, tpa, csize))
+    if rec is None or rec["sources"] != kernel_sources_digest():
+        return None
+    return rec["bytes"]
+
+
 def algorithmic_bytes(n, m, fallbacks, spm):
     """Bytes one iteration of one colony must touch (per ant-step, plus the
     full-scan fallback): candidate row (index 128 B + weight 128 B), the
@@ -228,6 +281,77 @@ def algorithmic_bytes(n, m, fallbacks, spm):
     return steps * per + fb
 
 
+GAP_EVAL = [("clustered", 2392, 301), ("uniform", 5000, 302), ("clustered", 5000, 303)]
+
+
+def gap_leg(iters, log=None):
+    """Tour-length gap at equal GPU time, learned prior vs plain.
+
+    Training: 500 generated instances (n in [200,1000], even b uniform, odd b
+    clustered), labels = best-tour edge frequencies of 4 plain-ACS runs x 100
+    iterations (m=64), 8 epochs of Adam on the library's MLP kernels.
+    Evaluation on held-out instances (n=2392 clustered, n=5000 uniform and
+    clustered), m=128, one batched context each: the plain colony runs `iters`
+    iterations; the prior colony (16 of 32 candidates, w' = w*p) gets the same
+    GPU time. The gap of a run is (L - L*)/L*, L* the best tour either found.
+    """
+    import torch
+
+    from paper_1605_02669_gb300 import acs, instances, prior
+
+    t0 = time.perf_counter()
+    params, losses = prior.train(n_instances=500, n_lo=200, n_hi=1000, runs=4, iters=100, m=64,
+                                 epochs=8, batch=4096, lr=2e-3, seed=11)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    sizes = [n for _, n, _ in GAP_EVAL]
+    xy = np.concatenate([instances.clustered(n, seed=s) if k == "clustered"
+                         else instances.uniform(n, seed=s) for k, n, s in GAP_EVAL])
+    off = np.zeros(len(sizes) + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    result = {}
+    budget = None
+    st = torch.cuda.Stream()
+    for mode in ("plain", "prior"):
+        col = acs.Colony(xy, acs.params(m=128, cl=32, seed=7), offsets=off)
+        if mode == "prior":
+            prior.apply(col, params, keep=16)
+        col.autotune(trial_iters=1)
+        col.set_stream(st.cuda_stream)     # the events below time the colony's own stream
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gpu_ms, done = 0.0, 0
+        while (budget is None and done < iters) or (budget is not None and gpu_ms < budget):
+            ev0.record(st)
+            col.run(10)
+            ev1.record(st)
+            ev1.synchronize()
+            gpu_ms += ev0.elapsed_time(ev1)
+            done += 10
+        if budget is None:
+            budget = gpu_ms
+        result[mode] = {"best": [int(col.best(b)[1]) for b in range(len(sizes))],
+                        "iterations": done, "gpu_ms": gpu_ms}
+        col.close()
+    best = [min(a, b) for a, b in zip(result["plain"]["best"], result["prior"]["best"])]
+    for mode in result:
+        result[mode]["gap"] = [(L - Ls) / Ls for L, Ls in zip(result[mode]["best"], best)]
+        result[mode]["mean_gap"] = float(np.mean(result[mode]["gap"]))
+    return {
+        "metric": "mean tour-length gap at equal GPU time (to the best tour either run found)",
+        "plain": result["plain"]["mean_gap"],
+        "prior": result["prior"]["mean_gap"],
+        "unit": "fraction",
+        "higher_is_better": False,
+        "instances": ["%s n=%d" % (k, n) for k, n, _ in GAP_EVAL],
+        "runs": result,
+        "plain_iterations": iters,
+        "m": 128,
+        "train": {"instances": 500, "n": [200, 1000], "label_runs": 4, "label_iters": 100,
+                  "epochs": 8, "final_loss": losses[-1], "seconds": t_train},
+    }
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -237,7 +361,8 @@ def run_ours(args, rank, world, local):
     import __graft_entry__
 
     __graft_entry__.build()
-    coords = make_coords(seed_offset=rank)
+    rs = rank_seed(rank)
+    coords = make_coords(seed_offset=rs["instances_seed_offset"])
     xy = np.concatenate(coords).astype(np.int32)
     off = np.zeros(len(coords) + 1, np.int64)
     off[1:] = np.cumsum([c.shape[0] for c in coords])
@@ -249,7 +374,7 @@ def run_ours(args, rank, world, local):
             "spm": (acs.ACS_MEM_SPM,)}[args.only]
     for mem, st in zip(mems, (sA, sB)):
         p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
-                       seed=1 + rank)
+                       seed=rs["philox_seed"])
         col = acs.Colony(xy, p, offsets=off)
         col.set_stream(st.cuda_stream)
         if args.tpa or args.cluster:
@@ -267,29 +392,30 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(record=None):
+        # ev0/ev1 bracket the step; kev[i] brackets colony i's launch on its own stream
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
-        evm0 = torch.cuda.Event(enable_timing=True)
-        evm1 = torch.cuda.Event(enable_timing=True)
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in ctxs]
         evb = torch.cuda.Event()
         ev0.record(sA)
         sB.wait_event(ev0)
-        evm0.record(sA)
-        ctxs[0][0].run(1)
-        evm1.record(sA)
+        for (col, st), (k0, k1) in zip(ctxs, kev):
+            k0.record(st)
+            col.run(1)
+            k1.record(st)
         if len(ctxs) > 1:
-            ctxs[1][0].run(1)
             evb.record(sB)
             sA.wait_event(evb)
         ev1.record(sA)
-        return ev0, ev1, evm0, evm1
+        return ev0, ev1, kev
 
     for _ in range(args.warmup):
         flush.zero_()
         torch.cuda.synchronize()
         step()
     torch.cuda.synchronize()
-    fb0 = [ctxs[0][0].stats(b)[0] for b in range(len(SIZES))]
+    fb0 = [[c.stats(b)[0] for b in range(len(SIZES))] for c, _ in ctxs]
     units_per_step = sum(M * (n - 1) for n in SIZES) * len(ctxs)
     if world > 1:
         import torch.distributed as dist
@@ -311,24 +437,37 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    step_ms = [e0.elapsed_time(e1) for e0, e1, _, _ in events]
-    mat_ms = [m0.elapsed_time(m1) for _, _, m0, m1 in events]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    fb1 = [ctxs[0][0].stats(b)[0] for b in range(len(SIZES))]
-    units = units_per_step * args.steps * world
-    value = units / (total_ms / 1000.0)
+    step_ms = [e0.elapsed_time(e1) for e0, e1, _ in events]
+    kern_ms = [[k0.elapsed_time(k1) for k0, k1 in kev] for _, _, kev in events]
+    total_ms = max_over_ranks(float(sum(step_ms)), world, "cuda")
+    fb1 = [[c.stats(b)[0] for b in range(len(SIZES))] for c, _ in ctxs]
+    value = job_throughput(units_per_step * args.steps, world, total_ms)
 
-    # dominant kernel: the matrix construct launch (both matrix instances)
-    fb_per_launch = [(b - a) / args.steps for a, b in zip(fb0, fb1)]
-    bytes_launch = sum(algorithmic_bytes(n, M, f, False) for n, f in zip(SIZES, fb_per_launch))
-    mat_avg_s = float(np.mean(mat_ms)) / 1000.0
-    achieved = bytes_launch / mat_avg_s / 1e9
+    # roofline of each colony's construct launch (both instances in one launch);
+    # the dominant kernel is the one with the longer average launch
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    roofs = []
+    for i, (col, _) in enumerate(ctxs):
+        spm = col.p.memory == acs.ACS_MEM_SPM
+        fb = [(b - a) / args.steps for a, b in zip(fb0[i], fb1[i])]
+        bytes_launch = sum(algorithmic_bytes(n, M, f, spm) for n, f in zip(SIZES, fb))
+        avg_s = float(np.mean([k[i] for k in kern_ms])) / 1000.0
+        achieved = bytes_launch / avg_s / 1e9
+        name = MEM_NAMES[col.p.memory]
+        t = tuning[name]
+        roofs.append({
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": kernel_traffic(name, t["threads_per_ant"], t["cluster_size"]),
+            "kernel": "construct_kernel<%d,%d> (%s, n=1002+2392 in one launch, clusters of %d)"
+                      % (t["threads_per_ant"], col.kernel_mode, name,
+                         t["cluster_size"]),
+            "peak_kind": peak_kind, "kernel_ms": 1000.0 * avg_s,
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "fallback_rate": float(sum(fb) / (M * sum(n - 1 for n in SIZES))),
+        })
+    roofs.sort(key=lambda r: -r["kernel_ms"])
 
     # end to end through the public API: host coordinates in, best tour out
     # every iteration (pinned host buffers not needed by the C ABI: it copies)
@@ -360,6 +499,7 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return None
+    gap = None if args.no_gap else gap_leg(args.gap_iters)
     cpu = None if args.no_cpu_baseline else cpu_baseline_leg()
     return {
         "metric": "ant-steps/s in tour construction",
@@ -376,20 +516,14 @@ def run_ours(args, rank, world, local):
         "data": "synthetic",
         "config": workload_config(),
         "iterations_per_s": 1000.0 * args.steps / total_ms,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "construct_kernel<%d,0> (matrix, n=1002+2392 in one launch, "
-                               "clusters of %d)" % (tuning["matrix"]["threads_per_ant"],
-                                                    tuning["matrix"]["cluster_size"])
-                     if "matrix" in tuning else "construct_kernel (SPM only)",
-                     "peak_kind": peak_kind,
-                     "kernel_ms": float(np.mean(mat_ms))},
+        "roofline": roofs[0],
+        "roofline_other": roofs[1:],
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(launches),
         "tuning": tuning,
-        "fallback_rate": float(sum(fb_per_launch) / (M * sum(n - 1 for n in SIZES))),
+        "gap_at_equal_time": gap,
     }
 
 
@@ -403,6 +537,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--only", choices=["both", "matrix", "spm"], default="both",
                     help="time only one memory kind (profiling runs; the metric needs both)")
+    ap.add_argument("--no-gap", action="store_true",
+                    help="skip the learned-prior gap leg (profiling runs)")
+    ap.add_argument("--gap-iters", type=int, default=1000,
+                    help="iterations of the plain colony in the gap leg")
     ap.add_argument("--tpa", type=int, default=0, help="pin lanes per ant instead of autotuning")
     ap.add_argument("--cluster", type=int, default=0, help="pin the cluster size instead of autotuning")
     args = ap.parse_args()

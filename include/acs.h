@@ -115,6 +115,12 @@ int32_t acs_threads_per_ant(const acs_ctx* ctx);
 acs_status acs_set_cluster_size(acs_ctx* ctx, int32_t csize);
 int32_t acs_cluster_size(const acs_ctx* ctx);
 
+/* Variant of the construct kernel the context launches (no counterpart in the
+ * paper; for profiling): 0 = pheromone matrix, 1 = SPM records in global
+ * memory, 2 = SPM records resident in the shared memory of the cluster for
+ * the launch. -1 for NULL. */
+int32_t acs_kernel_mode(const acs_ctx* ctx);
+
 /* Autotuner: for every (threads per ant, cluster size) pair that can launch,
  * times `trial_iters` iterations after one warm-up iteration, restoring the
  * full colony state after every trial, and keeps the fastest pair (written to

@@ -87,6 +87,8 @@ def load():
     L.acs_set_cluster_size.argtypes = [_vp, _i32]
     L.acs_cluster_size.argtypes = [_vp]
     L.acs_cluster_size.restype = _i32
+    L.acs_kernel_mode.argtypes = [_vp]
+    L.acs_kernel_mode.restype = _i32
     L.acs_prior_features.argtypes = [_vp, _i32, _vp, _vp]
     L.acs_prior_count_best_edges.argtypes = [_vp, _i32, _vp, _vp]
     L.acs_mlp_forward.argtypes = [_vp, _vp, _i64, _vp, _vp]
@@ -228,6 +230,10 @@ def acs_cluster_size(ctx):
     return int(load().acs_cluster_size(ctx))
 
 
+def acs_kernel_mode(ctx):
+    return int(load().acs_kernel_mode(ctx))
+
+
 def acs_autotune(ctx, trial_iters):
     tpa = np.zeros(1, np.int32)
     cs = np.zeros(1, np.int32)
@@ -336,6 +342,10 @@ class Colony:
     @property
     def cluster_size(self):
         return acs_cluster_size(self.ctx)
+
+    @property
+    def kernel_mode(self):
+        return acs_kernel_mode(self.ctx)
 
     @property
     def threads_per_ant(self):

@@ -679,6 +679,7 @@ acs_status acs_set_cluster_size(acs_ctx* c, int32_t csize)
 }
 
 int32_t acs_cluster_size(const acs_ctx* c) { return c ? c->csize : -1; }
+int32_t acs_kernel_mode(const acs_ctx* c) { return c ? c->mode : -1; }
 
 acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
                         int32_t* chosen_csize)

@@ -175,7 +175,8 @@ def train(n_instances=2000, n_lo=200, n_hi=1000, runs=8, iters=200, m=64, epochs
     (params tensor, per-epoch losses)."""
     xy, off, _, _ = instances.mixed_batch(n_instances, n_lo, n_hi, seed=seed)
     label = edge_labels(xy, off, runs=runs, iters=iters, m=m, seed=seed)
-    col = acs.Colony(xy, acs.params(m=1, cl=32, seed=seed), offsets=off)
+    # a one-ant SPM context only to hold the candidate lists for the features
+    col = acs.Colony(xy, acs.params(m=1, cl=32, memory=acs.ACS_MEM_SPM, seed=seed), offsets=off)
     feat = batch_features(col)
     col.close()
     tr = Trainer(init_params(seed), lr=lr)
@@ -186,3 +187,35 @@ def train(n_instances=2000, n_lo=200, n_hi=1000, runs=8, iters=200, m=64, epochs
         if log:
             log("epoch %d loss %.5f" % (e, losses[-1]))
     return tr.params, losses
+
+
+def main(argv=None):
+    """Train the prior on generated instances and save the parameter vector."""
+    import argparse
+    import time
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--instances", type=int, default=2000)
+    ap.add_argument("--n-lo", type=int, default=200)
+    ap.add_argument("--n-hi", type=int, default=1000)
+    ap.add_argument("--runs", type=int, default=8, help="plain-ACS runs per instance for labels")
+    ap.add_argument("--iters", type=int, default=200, help="iterations of each labelling run")
+    ap.add_argument("--m", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--seed", type=int, default=11)
+    ap.add_argument("--out", default="prior_params.npy")
+    a = ap.parse_args(argv)
+    from . import build
+
+    build.build()
+    t0 = time.time()
+    params, _ = train(a.instances, a.n_lo, a.n_hi, a.runs, a.iters, a.m, a.epochs, a.batch, a.lr,
+                      a.seed, log=print)
+    np.save(a.out, params.cpu().numpy())
+    print("trained in %.1f s -> %s" % (time.time() - t0, a.out))
+
+
+if __name__ == "__main__":
+    main()

@@ -95,3 +95,25 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(acs, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(ImportError):
         acs.load()
+
+
+def test_prior_calls_reject_bad_arguments_on_host(lib):
+    E = acs.ACS_EINVAL
+    vp = ctypes.c_void_p
+    fake = vp(0x1000)   # never dereferenced: every call below fails its checks first
+    assert lib.acs_prior_features(None, 0, fake, None) == E
+    assert lib.acs_prior_features(fake, 0, None, None) == E
+    assert lib.acs_prior_count_best_edges(None, 0, fake, None) == E
+    assert lib.acs_apply_prior(None, 0, fake, 16, None) == E
+    assert lib.acs_apply_prior(fake, 0, None, 16, None) == E
+    assert lib.acs_set_candidates(None, 0, fake, fake, 16) == E
+    assert lib.acs_mlp_forward(fake, fake, -1, fake, None) == E
+    assert lib.acs_mlp_forward(None, fake, 5, fake, None) == E
+    assert lib.acs_mlp_forward(None, None, 0, None, None) == acs.ACS_OK   # nothing to do
+    assert lib.acs_mlp_train_batch(fake, fake, fake, 0, 0, 1, 1, 0, fake, fake, None) == E
+    assert lib.acs_mlp_train_batch(fake, fake, fake, 10, 0, 0, 1, 0, fake, fake, None) == E
+    assert lib.acs_mlp_train_batch(fake, fake, fake, 10, 0, 4, 0, 0, fake, fake, None) == E
+    assert lib.acs_mlp_train_batch(fake, fake, None, 10, 0, 4, 1, 0, fake, fake, None) == E
+    assert lib.acs_mlp_adam(fake, fake, fake, fake, 0, 1e-3, 0.9, 0.999, 1e-8, None) == E
+    assert lib.acs_mlp_adam(None, fake, fake, fake, 1, 1e-3, 0.9, 0.999, 1e-8, None) == E
+    assert lib.acs_kernel_mode(None) == -1
