@@ -243,6 +243,7 @@ KERNEL_SOURCES = ["acs_construct.cu", "acs_device.cuh", "acs_internal.cuh"]
 # size) and valid only for the kernel sources they were taken on.
 CAPTURED_TRAFFIC = {
     ("matrix", 32, 16): {"bytes": 36976128 + 370432, "sources": "e541c7890bd7"},
+    ("spm", 32, 16): {"bytes": 16452096 + 0, "sources": "e541c7890bd7"},
 }
 
 
