@@ -262,7 +262,8 @@ acs_status fail_cuda(acs_ctx* c, cudaError_t e)
 // Shared-memory plan and block/grid of the construct launch for a
 // (threads-per-ant, cluster size) pair: each CTA of a cluster owns
 // mc = ceil(m/csize) ants, one group of tpa lanes per ant, at least one thread
-// per ant of the instance (the update phase), at most 1024 threads; as many
+// per ant of the instance (the update phase), at most 1024 threads (all 1024
+// when the clusters of all instances fit on the GPU at once); as many
 // clusters as fit on the GPU, at most one per instance.
 cudaError_t configure(acs_ctx* c, int tpa, int csize)
 {
@@ -296,6 +297,9 @@ cudaError_t configure(acs_ctx* c, int tpa, int csize)
         ACS_TRY(cudaStreamSynchronize(c->stream));
     }
     int block = std::max(mc * tpa, m);
+    // Spare warps speed up the full scan of the fallback: when every instance's
+    // cluster has SMs of its own, each CTA gets the full 1024 threads.
+    if ((long long)c->B * csize <= (long long)c->sms) block = 1024;
     block = std::min(1024, std::max(64, block));
     block = (block + 31) / 32 * 32;
     if (block < m) return cudaErrorInvalidConfiguration;

@@ -13,14 +13,12 @@
 //      and applies Eq. 1-2: a group argmax of tau*eta^beta (q < q0) or a
 //      Hillis-Steele roulette (Sec. 3.1.1). An ant whose candidate set is
 //      empty is queued.
-//   B  ants whose candidate set is empty are queued with the step's edges.
-//      After the first cluster barrier every CTA scans its 1/C slice of the
-//      nodes for every queued ant of the cluster (the ant's visited bits are
-//      read through distributed shared memory) and merges its partial argmax
-//      of tau*eta^beta (ties -> lowest node) in its own shared memory; after a
-//      second barrier the owner (and every CTA that needs the edge) takes the
-//      maximum of the C partial results: the block-level reduction of
-//      Sec. 3.1.1 spread over the cluster.
+//   B  after the step's selections every warp of the CTA scans all n nodes
+//      for the CTA's queued ants (split among them) and takes the argmax of
+//      tau*eta^beta over the unvisited ones (ties -> lowest node): the
+//      block-level reduction of Sec. 3.1.1. On the SPM the scan reads only
+//      the heuristic (every absent trail is tau0) and the record's own
+//      entries are offered with their stored trails.
 //   C  every CTA reads all m edges through distributed shared memory and
 //      counts equal undirected edges (no atomics: each edge is compared with
 //      all others by a few threads). An edge taken by k ants gets
@@ -57,7 +55,6 @@ struct Misc {
     unsigned long long stat[4];   // fallback, selections, spm hits, spm misses
     long long best_len;
     long long iteration;
-    int qoff[20];                 // prefix sums of the cluster's queues
     int nrel;                     // edges this CTA writes in the current step
 };
 
@@ -189,24 +186,6 @@ __device__ __forceinline__ void prefetch_l2(const void* p)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Maximum of entry `ent` over the C CTAs' partial results (C <= 16), loaded
-// four at a time.
-__device__ __forceinline__ unsigned long long cluster_max_entry(cg::cluster_group& cluster,
-                                                                unsigned long long* part, int ent,
-                                                                int C)
-{
-    unsigned long long key = 0ull;
-    for (int r0 = 0; r0 < C; r0 += 4) {
-        unsigned long long k[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            k[i] = r0 + i < C ? cluster.map_shared_rank(part, r0 + i)[ent] : 0ull;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) key = k[i] > key ? k[i] : key;
-    }
-    return key;
-}
-
 // MODE 0: pheromone matrix. MODE 1: SPM records in global memory. MODE 2: SPM
 // record r resident, for the launch, in the shared memory of CTA r mod C
 // (loaded at the start, written back after the global update); other CTAs
@@ -252,9 +231,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         uint32_t* pedge = (uint32_t*)(smem + L.pedge);   // (u << 16) | v, or queued | index
         int* qant = (int*)(smem + L.qant);
         int* qc = (int*)(smem + L.qc);
-        unsigned long long* qpart = (unsigned long long*)(smem + L.qpart);  // by cluster entry
-        int* eqc = (int*)(smem + L.eqc);
-        int* eqown = (int*)(smem + L.eqown);
+        unsigned long long* qpart = (unsigned long long*)(smem + L.qpart);  // by queue entry
         int* eqal = (int*)(smem + L.eqal);
         uint32_t* gkey = (uint32_t*)(smem + L.gkey);
         int* gu = (int*)(smem + L.gu);
@@ -263,8 +240,6 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         int* gcnt = (int*)(smem + L.gcnt);
         int* ev0 = (int*)(smem + L.ev0);
         int* ev1 = (int*)(smem + L.ev1);
-        int* fri = (int*)(smem + L.fri);
-        float* frv = (float*)(smem + L.frv);
         Misc* misc = (Misc*)(smem + L.misc);
         int32_t* ridx_s = (int32_t*)(smem + L.ridx);
         float* rval_s = (float*)(smem + L.rval);
@@ -378,9 +353,8 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                             const int qi = atomicAdd(qn, 1);
                             qant[qi] = al;
                             qc[qi] = c;
-                            pedge[al] = 0x80000000u | (uint32_t)qi;
                         }
-                        // the cluster scans row c after the barrier: stage it in L2
+                        // the CTA scans row c after the step's selections: stage it in L2
                         for (int j = gl * 32; j < n; j += TPA * 32) {
                             if constexpr (!SPM) prefetch_l2(tau + (size_t)c * n + j);
                             if (hw) prefetch_l2(hw + (size_t)c * n + j);
@@ -511,57 +485,42 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     if (upd && !SPM) s_tsel[al] = __ldcg(tau + (size_t)c * n + next);
                 }
             }
-            cluster.sync();   // the step's edges and queues are visible cluster-wide
-
-            // Phase B: the cluster's queued ants, argmax over all unvisited nodes
-            if (tid < 32) {
-                // lane r reads CTA r's queue length; inclusive warp scan
-                int cnt = tid < C ? cluster.map_shared_rank(&misc->qn[step & 1], tid)[0] : 0;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int o = __shfl_up_sync(0xffffffffu, cnt, off);
-                    if (tid >= off) cnt += o;
-                }
-                if (tid == 0) misc->qoff[0] = 0;
-                if (tid < C) misc->qoff[tid + 1] = cnt;
-            }
-            __syncthreads();
-            const int Q = misc->qoff[C];
-            if (Q > 0) {
-                // entry e of the cluster: owner CTA, owner's ant, current node
-                if (tid < Q) {
-                    int r = 0;
-                    while (misc->qoff[r + 1] <= tid) ++r;
-                    const int qi = tid - misc->qoff[r];
-                    qpart[tid] = 0ull;
-                    eqown[tid] = r;
-                    eqal[tid] = cluster.map_shared_rank(qant, r)[qi];
-                    const int c = cluster.map_shared_rank(qc, r)[qi];
-                    eqc[tid] = c;
-                }
+            // Phase B: this CTA's queued ants take the argmax of tau*eta^beta over
+            // all their unvisited nodes (Alg. 2, Sec. 3.1.1); every warp of the
+            // CTA scans, split among the queued ants
+            __syncthreads();   // the step's queue is complete
+            const int E = *qn;
+            if (E > 0) {
+                for (int e = tid; e < E; e += nthr) qpart[e] = 0ull;
                 __syncthreads();
                 if constexpr (SPM) {
-                    // stage the queued ants' records, one thread per (entry, slot)
-                    for (int k = tid; k < Q * s_slots; k += nthr) {
+                    // Stored trails are never below tau0 (local and global updates
+                    // move a trail towards tau0 or Delta > tau0 without crossing
+                    // it), so the scan below can take tau0 for every node: a
+                    // record's entries are offered here with their stored values,
+                    // and the largest product and its lowest node are unchanged.
+                    for (int k = tid; k < E * s_slots; k += nthr) {
                         const int e = k / s_slots, q2 = k - e * s_slots;
-                        const Rec R = rec(eqc[e]);
-                        fri[k] = ld_i<RG>(R.idx + q2);
-                        frv[k] = ld_f<RG>(R.val + q2);
+                        const int c = qc[e];
+                        const Rec R = rec(c);
+                        const int j = ld_i<RG>(R.idx + q2);
+                        if (j >= 0 && !visited(vis_base + (size_t)qant[e] * W, j)) {
+                            const float t = ld_f<RG>(R.val + q2);
+                            const float h = hw ? hw[(size_t)c * n + j]
+                                               : heuristic(euc2d(xy[c], xy[j]), A.beta);
+                            atomicMax(&qpart[e], pack_pj(__fmul_rn(t, h), j));
+                        }
                     }
-                    __syncthreads();
                 }
-                const int span = (n + C - 1) / C;
-                const int jlo = rank * span, jhi = min(n, jlo + span);
-                // warps are split among the entries so that all entries are
-                // scanned at once: with Q <= warps entry e gets the warps e,
-                // e+Q, ... (nwarps/Q of them); otherwise one warp per entry
+                // with E <= warps entry e gets the warps e, e+E, ... (warps/E of
+                // them); otherwise one warp per entry
                 const int nwarps = nthr >> 5, warp = tid >> 5;
-                const int wpe = Q <= nwarps ? nwarps / Q : 1;
-                for (int e = Q <= nwarps ? warp % Q : warp; e < Q; e += nwarps) {
-                    const int wi = Q <= nwarps ? warp / Q : 0;
+                const int wpe = E <= nwarps ? nwarps / E : 1;
+                for (int e = E <= nwarps ? warp % E : warp; e < E; e += nwarps) {
+                    const int wi = E <= nwarps ? warp / E : 0;
                     if (wi >= wpe) break;
-                    const int r = eqown[e], c = eqc[e];
-                    const uint32_t* vis = vis_of(r, eqal[e]);
+                    const int c = qc[e];
+                    const uint32_t* vis = vis_base + (size_t)qant[e] * W;
                     const float* trow = tau + (size_t)c * n;
                     const float* hrow = hw ? hw + (size_t)c * n : nullptr;
                     const int2 pc = xy[c];
@@ -569,7 +528,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     const int stride = wpe * 32;
                     // batches of four: every load of a batch is issued before the
                     // first is used
-                    for (int j0 = jlo + wi * 32 + lane; j0 < jhi; j0 += 4 * stride) {
+                    for (int j0 = wi * 32 + lane; j0 < n; j0 += 4 * stride) {
                         uint32_t word[4];
                         float t[4], h[4];
 #pragma unroll
@@ -578,7 +537,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                             word[i] = 0xffffffffu;
                             t[i] = tau0;
                             h[i] = 0.0f;
-                            if (j < jhi) {
+                            if (j < n) {
                                 word[i] = vis[j >> 5];
                                 if constexpr (!SPM) t[i] = __ldcg(trow + j);
                                 h[i] = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
@@ -587,39 +546,34 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int j = j0 + i * stride;
-                            if (j >= jhi || ((word[i] >> (j & 31)) & 1u)) continue;
-                            float tt = t[i];
-                            if constexpr (SPM) {
-                                for (int q2 = 0; q2 < s_slots; ++q2)
-                                    if (fri[e * s_slots + q2] == j) tt = frv[e * s_slots + q2];
-                            }
-                            const unsigned long long k2 = pack_pj(__fmul_rn(tt, h[i]), j);
+                            if (j >= n || ((word[i] >> (j & 31)) & 1u)) continue;
+                            const unsigned long long k2 = pack_pj(__fmul_rn(t[i], h[i]), j);
                             key = k2 > key ? k2 : key;
                         }
                     }
                     key = warp_max_u64(key);
                     if (lane == 0 && key != 0ull) atomicMax(&qpart[e], key);
-                    if (Q <= nwarps) break;
+                    if (E <= nwarps) break;
                 }
-                cluster.sync();   // every CTA's partial argmax is final
-                // owners finish their queued ants (folded into the edge gather
-                // when the step's edges are updated)
-                const int E = misc->qoff[rank + 1] - misc->qoff[rank];
-                for (int qi = tid; qi < E && !upd; qi += nthr) {
+                __syncthreads();
+                for (int qi = tid; qi < E; qi += nthr) {
                     const int al = qant[qi], c = qc[qi];
-                    const unsigned long long key = cluster_max_entry(cluster, qpart, misc->qoff[rank] + qi, C);
-                    const int next = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+                    const unsigned long long key = qpart[qi];
+                    int next = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
                     if (key == 0ull || next < 0 || next >= n) {
+                        // no unvisited node: cannot happen before step n
                         atomicExch(A.status, 4);
-                        continue;
+                        next = c;
                     }
                     s_nxt[al] = next;
                     if constexpr (!SPM) s_tsel[al] = __ldcg(tau + (size_t)c * n + next);
                     tours[(size_t)(a0 + al) * n + step] = next;
                     vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
+                    pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
                 }
                 if (tid == 0) n_fb += (unsigned long long)E;
             }
+            cluster.sync();   // the step's edges are visible cluster-wide
 
             // Phase C: folded local update of the step's distinct edges
             if (upd) {
@@ -629,27 +583,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     const int a = tid;
                     const int r = a / mc;
                     const uint32_t e = cluster.map_shared_rank(pedge, r)[a - r * mc];
-                    int u, v;
-                    if (e & 0x80000000u) {
-                        const int qi = (int)(e & 0xffffu);
-                        const unsigned long long key = cluster_max_entry(cluster, qpart, misc->qoff[r] + qi, C);
-                        u = cluster.map_shared_rank(qc, r)[qi];
-                        v = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
-                        if (key == 0ull || v < 0 || v >= n) {
-                            atomicExch(A.status, 4);
-                            v = u;
-                        } else if (r == rank) {
-                            // this CTA's own queued ant: finish its step
-                            const int al = a - a0;
-                            s_nxt[al] = v;
-                            if constexpr (!SPM) s_tsel[al] = __ldcg(tau + (size_t)u * n + v);
-                            tours[(size_t)a * n + step] = v;
-                            vis_base[(size_t)al * W + (v >> 5)] |= 1u << (v & 31);
-                        }
-                    } else {
-                        u = (int)(e >> 16);
-                        v = (int)(e & 0xffffu);
-                    }
+                    const int u = (int)(e >> 16), v = (int)(e & 0xffffu);
                     gkey[a] = (uint32_t)min(u, v) * (uint32_t)n + (uint32_t)max(u, v);
                     gu[a] = u;
                     gv[a] = v;
@@ -662,7 +596,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     if (tid < m) {
                         const int a = tid;
                         if ((gu[a] % C) == rank || (gv[a] % C) == rank)
-                            eqal[atomicAdd(&misc->nrel, 1)] = a;   // eqal is free again here
+                            eqal[atomicAdd(&misc->nrel, 1)] = a;
                     }
                     __syncthreads();
                 }

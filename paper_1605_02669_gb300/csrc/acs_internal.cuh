@@ -63,8 +63,8 @@ struct ConstructArgs {
 // the host (to size the launch) and on the device (to place the arrays).
 // mc = ants owned by one CTA of the cluster, m = ants of the instance.
 struct SmemLayout {
-    uint32_t P, cur, start, nxt, tsel, len, pedge, qant, qc, qpart, eqc, eqown, eqal, gkey, gu,
-        gv, grep, gcnt, ev0, ev1, fri, frv, misc, ridx, rval, rtail, vis, xy, total;
+    uint32_t P, cur, start, nxt, tsel, len, pedge, qant, qc, qpart, eqal, gkey, gu, gv, grep, gcnt,
+        ev0, ev1, misc, ridx, rval, rtail, vis, xy, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -86,9 +86,7 @@ __host__ __device__ inline SmemLayout smem_layout(int m, int mc, int nrec, int s
     L.pedge = o; o = align16(o + 4u * mc);
     L.qant = o;  o = align16(o + 4u * mc);
     L.qc = o;    o = align16(o + 4u * mc);
-    L.qpart = o; o = align16(o + 8u * m);
-    L.eqc = o;   o = align16(o + 4u * m);
-    L.eqown = o; o = align16(o + 4u * m);
+    L.qpart = o; o = align16(o + 8u * mc);
     L.eqal = o;  o = align16(o + 4u * m);
     L.gkey = o;  o = align16(o + 4u * m);
     L.gu = o;    o = align16(o + 4u * m);
@@ -97,8 +95,6 @@ __host__ __device__ inline SmemLayout smem_layout(int m, int mc, int nrec, int s
     L.gcnt = o;  o = align16(o + 4u * m);
     L.ev0 = o;   o = align16(o + 4u * m);
     L.ev1 = o;   o = align16(o + 4u * m);
-    L.fri = o;   o = align16(o + 4u * (uint32_t)m * (uint32_t)s);
-    L.frv = o;   o = align16(o + 4u * (uint32_t)m * (uint32_t)s);
     L.misc = o;  o = align16(o + 256u);
     L.ridx = o;  o = align16(o + 4u * (uint32_t)nrec * (uint32_t)s);
     L.rval = o;  o = align16(o + 4u * (uint32_t)nrec * (uint32_t)s);
