@@ -56,6 +56,7 @@ struct Misc {
     long long best_len;
     long long iteration;
     int nrel;                     // edges this CTA writes in the current step
+    int work;                     // next phase-B item to claim
 };
 
 __device__ __forceinline__ bool visited(const uint32_t* vis, int j)
@@ -226,7 +227,6 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         int* s_cur = (int*)(smem + L.cur);
         int* s_start = (int*)(smem + L.start);
         int* s_nxt = (int*)(smem + L.nxt);
-        float* s_tsel = (float*)(smem + L.tsel);
         long long* s_len = (long long*)(smem + L.len);
         uint32_t* pedge = (uint32_t*)(smem + L.pedge);   // (u << 16) | v, or queued | index
         int* qant = (int*)(smem + L.qant);
@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         if (tid == 0) {
             misc->qn[0] = 0;
             misc->qn[1] = 0;
+            misc->work = 0;
             misc->best_len = __ldcg(A.best_len + b);
             misc->iteration = __ldcg(A.iteration + b);
             for (int i = 0; i < 4; ++i) misc->stat[i] = 0ull;
@@ -327,19 +328,19 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
             int* qn = &misc->qn[step & 1];
 
             if (!closing) {
-                // Phase A: pseudo-random-proportional rule on the candidate list
-                for (int al = group; al < ml; al += ngroups) {
+                // Phase A: pseudo-random-proportional rule on the candidate list.
+                // stage(): candidate row, visited bits and the step's Philox draw;
+                // an ant whose candidate set is empty is queued for phase B.
+                auto stage = [&](int al, int& c, int (&nv)[V], float (&wv)[V], bool (&unv)[V],
+                                 uint4& x) -> bool {
                     const int a = a0 + al;
-                    const int c = s_cur[al];
+                    c = s_cur[al];
                     const uint32_t* vis = vis_base + (size_t)al * W;
-                    int nv[V];
-                    float wv[V];
                     load_row<V>(nn_rows + (size_t)c * 32 + gl * V, w_rows + (size_t)c * 32 + gl * V,
                                 nv, wv);
                     // drawn here so that the rounds overlap the loads' latency
-                    const uint4 x = philox4x32_10(make_uint4(it, (uint32_t)a, (uint32_t)step, inst),
-                                                  A.key0, A.key1);
-                    bool unv[V];
+                    x = philox4x32_10(make_uint4(it, (uint32_t)a, (uint32_t)step, inst), A.key0,
+                                      A.key1);
                     bool lane_any = false;
 #pragma unroll
                     for (int i = 0; i < V; ++i) {
@@ -348,19 +349,24 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                         lane_any |= unv[i];
                     }
                     const unsigned anyb = __ballot_sync(gmask, lane_any) & gmask;
-                    if (anyb == 0u) {
-                        if (gl == 0) {
-                            const int qi = atomicAdd(qn, 1);
-                            qant[qi] = al;
-                            qc[qi] = c;
-                        }
-                        // the CTA scans row c after the step's selections: stage it in L2
-                        for (int j = gl * 32; j < n; j += TPA * 32) {
-                            if constexpr (!SPM) prefetch_l2(tau + (size_t)c * n + j);
-                            if (hw) prefetch_l2(hw + (size_t)c * n + j);
-                        }
-                        continue;
+                    if (anyb != 0u) return true;
+                    if (gl == 0) {
+                        const int qi = atomicAdd(qn, 1);
+                        qant[qi] = al;
+                        qc[qi] = c;
+                        qpart[qi] = 0ull;
                     }
+                    // phase B scans row c: stage it in L2
+                    for (int j = gl * 32; j < n; j += TPA * 32) {
+                        if constexpr (!SPM) prefetch_l2(tau + (size_t)c * n + j);
+                        if (hw) prefetch_l2(hw + (size_t)c * n + j);
+                    }
+                    return false;
+                };
+                // choose(): Eq. 1 or Eq. 2 over the unvisited candidates
+                auto choose = [&](int al, int c, const int (&nv)[V], const float (&wv)[V],
+                                  const bool (&unv)[V], const uint4& x) {
+                    const int a = a0 + al;
                     float tv[V];
                     if constexpr (!SPM) {
                         const float* trow = tau + (size_t)c * n;
@@ -462,19 +468,120 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     // broadcast the chosen node and its pheromone from the owning lane
                     const int owner = kpick / V, ii = kpick - owner * V;
                     int myn = nv[0];
-                    float myt = tv[0];
 #pragma unroll
                     for (int i = 1; i < V; ++i)
-                        if (ii == i) { myn = nv[i]; myt = tv[i]; }
+                        if (ii == i) myn = nv[i];
                     const int next = __shfl_sync(gmask, myn, owner, TPA);
-                    const float tsel = __shfl_sync(gmask, myt, owner, TPA);
                     if (gl == 0) {
                         s_nxt[al] = next;
-                        s_tsel[al] = tsel;
                         pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
                         tours[(size_t)a * n + step] = next;
                         vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
                     }
+                };
+                if (ml <= ngroups) {
+                    // at most one ant per group: the queue is published by a CTA
+                    // barrier between the two halves, so that warps without a
+                    // selection to make start the full scans at once
+                    const int al = group;
+                    int c = 0, nv[V];
+                    float wv[V];
+                    bool unv[V];
+                    uint4 x;
+                    bool busy = false;
+                    if (al < ml) busy = stage(al, c, nv, wv, unv, x);
+                    __syncthreads();   // the step's queue is complete
+                    if (busy) choose(al, c, nv, wv, unv, x);
+                } else {
+                    for (int al = group; al < ml; al += ngroups) {
+                        int c = 0, nv[V];
+                        float wv[V];
+                        bool unv[V];
+                        uint4 x;
+                        if (stage(al, c, nv, wv, unv, x)) choose(al, c, nv, wv, unv, x);
+                    }
+                    __syncthreads();   // the step's queue is complete
+                }
+                __syncwarp();
+
+                // Phase B: the CTA's queued ants take the argmax of tau*eta^beta
+                // over all their unvisited nodes (Alg. 2, Sec. 3.1.1). The scan is
+                // cut into items of 128 nodes of one queued ant; warps claim items
+                // from a shared counter as soon as their selections are done.
+                const int E = *qn;
+                const int nch = (n + 127) >> 7;
+                const int items = E * nch;
+                for (;;) {
+                    int item = 0;
+                    if (lane == 0) item = atomicAdd(&misc->work, 1);
+                    item = __shfl_sync(0xffffffffu, item, 0);
+                    if (item >= items) break;
+                    const int e = item / nch, ch = item - e * nch;
+                    const int c = qc[e];
+                    const uint32_t* vis = vis_base + (size_t)qant[e] * W;
+                    const float* trow = tau + (size_t)c * n;
+                    const float* hrow = hw ? hw + (size_t)c * n : nullptr;
+                    const int2 pc = xy[c];
+                    unsigned long long key = 0ull;
+                    uint32_t word[4];
+                    float t[4], h[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int j = (ch << 7) + i * 32 + lane;
+                        word[i] = 0xffffffffu;
+                        t[i] = tau0;
+                        h[i] = 0.0f;
+                        if (j < n) {
+                            word[i] = vis[j >> 5];
+                            if constexpr (!SPM) t[i] = __ldcg(trow + j);
+                            h[i] = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int j = (ch << 7) + i * 32 + lane;
+                        if (j >= n || ((word[i] >> (j & 31)) & 1u)) continue;
+                        const unsigned long long k2 = pack_pj(__fmul_rn(t[i], h[i]), j);
+                        key = k2 > key ? k2 : key;
+                    }
+                    if constexpr (SPM) {
+                        // Stored trails are never below tau0 (local and global
+                        // updates move a trail towards tau0 or Delta > tau0 without
+                        // crossing it), so the scan takes tau0 for every node and
+                        // the record's own entries are offered with their stored
+                        // trails: the largest product and its lowest node are the
+                        // same as with every trail read from the record.
+                        if (ch == 0 && lane < s_slots) {
+                            const Rec R = rec(c);
+                            const int j = ld_i<RG>(R.idx + lane);
+                            if (j >= 0 && !visited(vis, j)) {
+                                const float tr = ld_f<RG>(R.val + lane);
+                                const float hj = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
+                                const unsigned long long k2 = pack_pj(__fmul_rn(tr, hj), j);
+                                key = k2 > key ? k2 : key;
+                            }
+                        }
+                    }
+                    key = warp_max_u64(key);
+                    if (lane == 0 && key != 0ull) atomicMax(&qpart[e], key);
+                }
+                if (E > 0) {
+                    __syncthreads();   // every item is merged
+                    for (int qi = tid; qi < E; qi += nthr) {
+                        const int al = qant[qi], c = qc[qi];
+                        const unsigned long long key = qpart[qi];
+                        int next = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+                        if (key == 0ull || next < 0 || next >= n) {
+                            // no unvisited node: cannot happen before step n
+                            atomicExch(A.status, 4);
+                            next = c;
+                        }
+                        s_nxt[al] = next;
+                        tours[(size_t)(a0 + al) * n + step] = next;
+                        vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
+                        pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
+                    }
+                    if (tid == 0) n_fb += (unsigned long long)E;
                 }
             } else {
                 // closing edges (step n): last node back to the first
@@ -482,101 +589,21 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     const int c = s_cur[al], next = s_start[al];
                     s_nxt[al] = next;
                     pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
-                    if (upd && !SPM) s_tsel[al] = __ldcg(tau + (size_t)c * n + next);
                 }
-            }
-            // Phase B: this CTA's queued ants take the argmax of tau*eta^beta over
-            // all their unvisited nodes (Alg. 2, Sec. 3.1.1); every warp of the
-            // CTA scans, split among the queued ants
-            __syncthreads();   // the step's queue is complete
-            const int E = *qn;
-            if (E > 0) {
-                for (int e = tid; e < E; e += nthr) qpart[e] = 0ull;
-                __syncthreads();
-                if constexpr (SPM) {
-                    // Stored trails are never below tau0 (local and global updates
-                    // move a trail towards tau0 or Delta > tau0 without crossing
-                    // it), so the scan below can take tau0 for every node: a
-                    // record's entries are offered here with their stored values,
-                    // and the largest product and its lowest node are unchanged.
-                    for (int k = tid; k < E * s_slots; k += nthr) {
-                        const int e = k / s_slots, q2 = k - e * s_slots;
-                        const int c = qc[e];
-                        const Rec R = rec(c);
-                        const int j = ld_i<RG>(R.idx + q2);
-                        if (j >= 0 && !visited(vis_base + (size_t)qant[e] * W, j)) {
-                            const float t = ld_f<RG>(R.val + q2);
-                            const float h = hw ? hw[(size_t)c * n + j]
-                                               : heuristic(euc2d(xy[c], xy[j]), A.beta);
-                            atomicMax(&qpart[e], pack_pj(__fmul_rn(t, h), j));
-                        }
-                    }
-                }
-                // with E <= warps entry e gets the warps e, e+E, ... (warps/E of
-                // them); otherwise one warp per entry
-                const int nwarps = nthr >> 5, warp = tid >> 5;
-                const int wpe = E <= nwarps ? nwarps / E : 1;
-                for (int e = E <= nwarps ? warp % E : warp; e < E; e += nwarps) {
-                    const int wi = E <= nwarps ? warp / E : 0;
-                    if (wi >= wpe) break;
-                    const int c = qc[e];
-                    const uint32_t* vis = vis_base + (size_t)qant[e] * W;
-                    const float* trow = tau + (size_t)c * n;
-                    const float* hrow = hw ? hw + (size_t)c * n : nullptr;
-                    const int2 pc = xy[c];
-                    unsigned long long key = 0ull;
-                    const int stride = wpe * 32;
-                    // batches of four: every load of a batch is issued before the
-                    // first is used
-                    for (int j0 = wi * 32 + lane; j0 < n; j0 += 4 * stride) {
-                        uint32_t word[4];
-                        float t[4], h[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int j = j0 + i * stride;
-                            word[i] = 0xffffffffu;
-                            t[i] = tau0;
-                            h[i] = 0.0f;
-                            if (j < n) {
-                                word[i] = vis[j >> 5];
-                                if constexpr (!SPM) t[i] = __ldcg(trow + j);
-                                h[i] = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
-                            }
-                        }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int j = j0 + i * stride;
-                            if (j >= n || ((word[i] >> (j & 31)) & 1u)) continue;
-                            const unsigned long long k2 = pack_pj(__fmul_rn(t[i], h[i]), j);
-                            key = k2 > key ? k2 : key;
-                        }
-                    }
-                    key = warp_max_u64(key);
-                    if (lane == 0 && key != 0ull) atomicMax(&qpart[e], key);
-                    if (E <= nwarps) break;
-                }
-                __syncthreads();
-                for (int qi = tid; qi < E; qi += nthr) {
-                    const int al = qant[qi], c = qc[qi];
-                    const unsigned long long key = qpart[qi];
-                    int next = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
-                    if (key == 0ull || next < 0 || next >= n) {
-                        // no unvisited node: cannot happen before step n
-                        atomicExch(A.status, 4);
-                        next = c;
-                    }
-                    s_nxt[al] = next;
-                    if constexpr (!SPM) s_tsel[al] = __ldcg(tau + (size_t)c * n + next);
-                    tours[(size_t)(a0 + al) * n + step] = next;
-                    vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
-                    pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
-                }
-                if (tid == 0) n_fb += (unsigned long long)E;
             }
             cluster.sync();   // the step's edges are visible cluster-wide
 
             // Phase C: folded local update of the step's distinct edges
             if (upd) {
+                // the current trail of this CTA's own edges (matrix): nobody
+                // writes them before this CTA applies the update below
+                float t_own = 0.0f;
+                if constexpr (!SPM) {
+                    if (tid < ml) {
+                        const uint32_t e = pedge[tid];
+                        t_own = __ldcg(tau + (size_t)(e >> 16) * n + (e & 0xffffu));
+                    }
+                }
                 // every CTA gathers all m edges (one thread per ant: m <= nthr)
                 if (tid == 0) misc->nrel = 0;
                 if (tid < m) {
@@ -633,10 +660,10 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                 __syncthreads();
                 if constexpr (!SPM) {
                     // the CTA of the lowest ant on an edge writes both halves
-                    for (int al = tid; al < ml; al += nthr) {
-                        const int a = a0 + al;
+                    if (tid < ml) {
+                        const int a = a0 + tid;
                         if (grep[a] == a) {
-                            const float t2 = local_rule(s_tsel[al], tau0, sP[gcnt[a]]);
+                            const float t2 = local_rule(t_own, tau0, sP[gcnt[a]]);
                             const int u = gu[a], v = gv[a];
                             tau[(size_t)u * n + v] = t2;
                             tau[(size_t)v * n + u] = t2;
@@ -698,7 +725,10 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
             for (int al = tid; al < ml; al += nthr) s_cur[al] = s_nxt[al];
             // the queue counter of the next step was last read before the
             // previous barrier, so it can be cleared now
-            if (tid == 0) misc->qn[(step + 1) & 1] = 0;
+            if (tid == 0) {
+                misc->qn[(step + 1) & 1] = 0;
+                misc->work = 0;
+            }
             cluster.sync();
         }
 
