@@ -376,13 +376,31 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                         const Rec R = rec(c);
 #pragma unroll
                         for (int i = 0; i < V; ++i) tv[i] = tau0;
-#pragma unroll 8
-                        for (int q = 0; q < s_slots; ++q) {
-                            const int j = ld_i<RG>(R.idx + q);
-                            const float t = ld_f<RG>(R.val + q);
+                        if (s_slots <= TPA) {
+                            // lane q of the group loads slot q (one round trip);
+                            // the group sees every slot through shuffles
+                            int sj = -1;
+                            float st = 0.0f;
+                            if (gl < s_slots) {
+                                sj = ld_i<RG>(R.idx + gl);
+                                st = ld_f<RG>(R.val + gl);
+                            }
+                            for (int q = 0; q < s_slots; ++q) {
+                                const int j = __shfl_sync(gmask, sj, q, TPA);
+                                const float t = __shfl_sync(gmask, st, q, TPA);
 #pragma unroll
-                            for (int i = 0; i < V; ++i)
-                                if (nv[i] == j) tv[i] = t;
+                                for (int i = 0; i < V; ++i)
+                                    if (nv[i] == j) tv[i] = t;
+                            }
+                        } else {
+#pragma unroll 8
+                            for (int q = 0; q < s_slots; ++q) {
+                                const int j = ld_i<RG>(R.idx + q);
+                                const float t = ld_f<RG>(R.val + q);
+#pragma unroll
+                                for (int i = 0; i < V; ++i)
+                                    if (nv[i] == j) tv[i] = t;
+                            }
                         }
                     }
                     float v[V];
@@ -620,10 +638,15 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                 // ants' edges, on the SPM the edges that touch one of its records
                 // (their events are the only ones replayed here).
                 if constexpr (SPM) {
-                    if (tid < m) {
+                    // compaction with one shared-memory atomic per warp
+                    if (tid < ((m + 31) & ~31)) {
                         const int a = tid;
-                        if ((gu[a] % C) == rank || (gv[a] % C) == rank)
-                            eqal[atomicAdd(&misc->nrel, 1)] = a;
+                        const bool rel = a < m && ((gu[a] % C) == rank || (gv[a] % C) == rank);
+                        const unsigned bal = __ballot_sync(0xffffffffu, rel);
+                        int base = 0;
+                        if (lane == 0 && bal) base = atomicAdd(&misc->nrel, __popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (rel) eqal[base + __popc(bal & ((1u << lane) - 1u))] = a;
                     }
                     __syncthreads();
                 }
