@@ -180,6 +180,19 @@ __device__ __forceinline__ int seg_min(int v, int T)
     return v;
 }
 
+// The two halves of a cluster barrier: arrive (release: this thread's prior
+// writes become visible to the cluster) and wait (acquire). Work placed
+// between them overlaps the barrier's latency.
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // Bring the line holding p into L2 (no register result, no L1 fill: other SMs
 // may write the line before it is read).
 __device__ __forceinline__ void prefetch_l2(const void* p)
@@ -320,203 +333,211 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         cluster.sync();
 
         unsigned long long n_fb = 0, n_hit = 0, n_miss = 0;
+        // node of ant al after step s: nodeb[s & 1][al]
+        int* const nodeb[2] = {s_cur, s_nxt};
+        // Phase A: pseudo-random-proportional rule on the candidate list.
+        // stage(): candidate row, visited bits and the step's Philox draw;
+        // an ant whose candidate set is empty is queued for phase B.
+        auto stage = [&](int stp, int al, int& c, int (&nv)[V], float (&wv)[V],
+                         bool (&unv)[V], uint4& x) -> bool {
+            const int a = a0 + al;
+            c = nodeb[(stp - 1) & 1][al];
+            const uint32_t* vis = vis_base + (size_t)al * W;
+            load_row<V>(nn_rows + (size_t)c * 32 + gl * V, w_rows + (size_t)c * 32 + gl * V,
+                        nv, wv);
+            // drawn here so that the rounds overlap the loads' latency
+            x = philox4x32_10(make_uint4(it, (uint32_t)a, (uint32_t)stp, inst), A.key0,
+                              A.key1);
+            bool lane_any = false;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const int k = gl * V + i;
+                unv[i] = (k < cl) && !visited(vis, nv[i]);
+                lane_any |= unv[i];
+            }
+            const unsigned anyb = __ballot_sync(gmask, lane_any) & gmask;
+            if (anyb != 0u) return true;
+            if (gl == 0) {
+                const int qi = atomicAdd(&misc->qn[stp & 1], 1);
+                qant[qi] = al;
+                qc[qi] = c;
+                qpart[qi] = 0ull;
+            }
+            // phase B scans row c: stage it in L2
+            for (int j = gl * 32; j < n; j += TPA * 32) {
+                if constexpr (!SPM) prefetch_l2(tau + (size_t)c * n + j);
+                if (hw) prefetch_l2(hw + (size_t)c * n + j);
+            }
+            return false;
+        };
+        // choose(): Eq. 1 or Eq. 2 over the unvisited candidates
+        auto choose = [&](int stp, int al, int c, const int (&nv)[V], const float (&wv)[V],
+                          const bool (&unv)[V], const uint4& x) {
+            const int a = a0 + al;
+            float tv[V];
+            if constexpr (!SPM) {
+                const float* trow = tau + (size_t)c * n;
+#pragma unroll
+                for (int i = 0; i < V; ++i) tv[i] = unv[i] ? __ldcg(trow + nv[i]) : 0.0f;
+            } else {
+                const Rec R = rec(c);
+#pragma unroll
+                for (int i = 0; i < V; ++i) tv[i] = tau0;
+                if (s_slots <= TPA) {
+                    // lane q of the group loads slot q (one round trip);
+                    // the group sees every slot through shuffles
+                    int sj = -1;
+                    float st = 0.0f;
+                    if (gl < s_slots) {
+                        sj = ld_i<RG>(R.idx + gl);
+                        st = ld_f<RG>(R.val + gl);
+                    }
+                    for (int q = 0; q < s_slots; ++q) {
+                        const int j = __shfl_sync(gmask, sj, q, TPA);
+                        const float t = __shfl_sync(gmask, st, q, TPA);
+#pragma unroll
+                        for (int i = 0; i < V; ++i)
+                            if (nv[i] == j) tv[i] = t;
+                    }
+                } else {
+#pragma unroll 8
+                    for (int q = 0; q < s_slots; ++q) {
+                        const int j = ld_i<RG>(R.idx + q);
+                        const float t = ld_f<RG>(R.val + q);
+#pragma unroll
+                        for (int i = 0; i < V; ++i)
+                            if (nv[i] == j) tv[i] = t;
+                    }
+                }
+            }
+            float v[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) v[i] = unv[i] ? __fmul_rn(tv[i], wv[i]) : 0.0f;
+
+            const float q = unit24(x.x);
+            int kpick;
+            if (q < A.q0) {
+                // exploitation: argmax of tau*eta^beta, ties -> lowest rank.
+                // Non-negative floats order like their bit patterns.
+                uint32_t mb = 0u;
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (unv[i]) mb = max(mb, __float_as_uint(v[i]));
+#pragma unroll
+                for (int off = TPA / 2; off >= 1; off >>= 1)
+                    mb = max(mb, __shfl_xor_sync(gmask, mb, off, TPA));
+                int first = -1;
+#pragma unroll
+                for (int i = V - 1; i >= 0; --i)
+                    if (unv[i] && __float_as_uint(v[i]) == mb) first = i;
+                const unsigned bf = __ballot_sync(gmask, first >= 0) & gmask;
+                const int src = __ffs(bf) - 1 - gbase;
+                kpick = src * V + __shfl_sync(gmask, first, src, TPA);
+            } else {
+                // exploration: roulette of Eq. 2 over a 32-position
+                // inclusive Hillis-Steele scan (offsets 1,2,4,8,16)
+                const float r = unit24(x.y);
+                float P[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) P[i] = v[i];
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    float y[V];
+                    if (off >= V) {
+                        const int dl = off / V;
+#pragma unroll
+                        for (int i = 0; i < V; ++i) {
+                            const float o = __shfl_up_sync(gmask, P[i], dl, TPA);
+                            y[i] = gl >= dl ? __fadd_rn(P[i], o) : P[i];
+                        }
+                    } else {
+                        float prev[V];
+#pragma unroll
+                        for (int i = 0; i < V; ++i) {
+                            // positions i < off read the previous lane's V-off+i
+                            if (i < off) prev[i] = __shfl_up_sync(gmask, P[i - off + V], 1, TPA);
+                        }
+#pragma unroll
+                        for (int i = 0; i < V; ++i) {
+                            if (i >= off) y[i] = __fadd_rn(P[i], P[i - off]);
+                            else y[i] = gl >= 1 ? __fadd_rn(P[i], prev[i]) : P[i];
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < V; ++i) P[i] = y[i];
+                }
+                const float total = __shfl_sync(gmask, P[V - 1], TPA - 1, TPA);
+                const float t = __fmul_rn(r, total);
+                int first = -1, last = -1, firstu = -1;
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const bool pos = unv[i] && v[i] > 0.0f;
+                    if (first < 0 && pos && P[i] > t) first = i;
+                    if (pos) last = i;
+                    if (firstu < 0 && unv[i]) firstu = i;
+                }
+                const unsigned bf = __ballot_sync(gmask, first >= 0) & gmask;
+                const unsigned bl = __ballot_sync(gmask, last >= 0) & gmask;
+                const unsigned bu = __ballot_sync(gmask, firstu >= 0) & gmask;
+                if (bf) {
+                    const int src = __ffs(bf) - 1 - gbase;
+                    kpick = src * V + __shfl_sync(gmask, first, src, TPA);
+                } else if (bl) {
+                    const int src = 31 - __clz(bl) - gbase;
+                    kpick = src * V + __shfl_sync(gmask, last, src, TPA);
+                } else {
+                    const int src = __ffs(bu) - 1 - gbase;
+                    kpick = src * V + __shfl_sync(gmask, firstu, src, TPA);
+                }
+            }
+            // broadcast the chosen node and its pheromone from the owning lane
+            const int owner = kpick / V, ii = kpick - owner * V;
+            int myn = nv[0];
+#pragma unroll
+            for (int i = 1; i < V; ++i)
+                if (ii == i) myn = nv[i];
+            const int next = __shfl_sync(gmask, myn, owner, TPA);
+            if (gl == 0) {
+                nodeb[stp & 1][al] = next;
+                pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
+                tours[(size_t)a * n + stp] = next;
+                vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
+            }
+        };
+        // at most one ant per group ("split" steps): the group stages the coming
+        // step's candidate row during the barrier that ends a step
+        const bool split = ml <= ngroups;
+        int st_c = 0, st_nv[V];
+        float st_wv[V];
+        bool st_unv[V];
+        uint4 st_x = make_uint4(0u, 0u, 0u, 0u);
+        bool st_busy = false;
+        if (split && n > 1 && group < ml) st_busy = stage(1, group, st_c, st_nv, st_wv, st_unv, st_x);
+        __syncthreads();   // step 1's queue is complete
 
         // ---- steps 1 .. n (n = the closing edges)
         for (int step = 1; step <= n; ++step) {
             const bool closing = (step == n);
             const bool upd = (step % A.period) == 0;
             int* qn = &misc->qn[step & 1];
+            // the next step's queue counter was last read before the barrier
+            // that ended phase B of the previous step
+            if (tid == 0) misc->qn[(step + 1) & 1] = 0;
 
             if (!closing) {
-                // Phase A: pseudo-random-proportional rule on the candidate list.
-                // stage(): candidate row, visited bits and the step's Philox draw;
-                // an ant whose candidate set is empty is queued for phase B.
-                auto stage = [&](int al, int& c, int (&nv)[V], float (&wv)[V], bool (&unv)[V],
-                                 uint4& x) -> bool {
-                    const int a = a0 + al;
-                    c = s_cur[al];
-                    const uint32_t* vis = vis_base + (size_t)al * W;
-                    load_row<V>(nn_rows + (size_t)c * 32 + gl * V, w_rows + (size_t)c * 32 + gl * V,
-                                nv, wv);
-                    // drawn here so that the rounds overlap the loads' latency
-                    x = philox4x32_10(make_uint4(it, (uint32_t)a, (uint32_t)step, inst), A.key0,
-                                      A.key1);
-                    bool lane_any = false;
-#pragma unroll
-                    for (int i = 0; i < V; ++i) {
-                        const int k = gl * V + i;
-                        unv[i] = (k < cl) && !visited(vis, nv[i]);
-                        lane_any |= unv[i];
-                    }
-                    const unsigned anyb = __ballot_sync(gmask, lane_any) & gmask;
-                    if (anyb != 0u) return true;
-                    if (gl == 0) {
-                        const int qi = atomicAdd(qn, 1);
-                        qant[qi] = al;
-                        qc[qi] = c;
-                        qpart[qi] = 0ull;
-                    }
-                    // phase B scans row c: stage it in L2
-                    for (int j = gl * 32; j < n; j += TPA * 32) {
-                        if constexpr (!SPM) prefetch_l2(tau + (size_t)c * n + j);
-                        if (hw) prefetch_l2(hw + (size_t)c * n + j);
-                    }
-                    return false;
-                };
-                // choose(): Eq. 1 or Eq. 2 over the unvisited candidates
-                auto choose = [&](int al, int c, const int (&nv)[V], const float (&wv)[V],
-                                  const bool (&unv)[V], const uint4& x) {
-                    const int a = a0 + al;
-                    float tv[V];
-                    if constexpr (!SPM) {
-                        const float* trow = tau + (size_t)c * n;
-#pragma unroll
-                        for (int i = 0; i < V; ++i) tv[i] = unv[i] ? __ldcg(trow + nv[i]) : 0.0f;
-                    } else {
-                        const Rec R = rec(c);
-#pragma unroll
-                        for (int i = 0; i < V; ++i) tv[i] = tau0;
-                        if (s_slots <= TPA) {
-                            // lane q of the group loads slot q (one round trip);
-                            // the group sees every slot through shuffles
-                            int sj = -1;
-                            float st = 0.0f;
-                            if (gl < s_slots) {
-                                sj = ld_i<RG>(R.idx + gl);
-                                st = ld_f<RG>(R.val + gl);
-                            }
-                            for (int q = 0; q < s_slots; ++q) {
-                                const int j = __shfl_sync(gmask, sj, q, TPA);
-                                const float t = __shfl_sync(gmask, st, q, TPA);
-#pragma unroll
-                                for (int i = 0; i < V; ++i)
-                                    if (nv[i] == j) tv[i] = t;
-                            }
-                        } else {
-#pragma unroll 8
-                            for (int q = 0; q < s_slots; ++q) {
-                                const int j = ld_i<RG>(R.idx + q);
-                                const float t = ld_f<RG>(R.val + q);
-#pragma unroll
-                                for (int i = 0; i < V; ++i)
-                                    if (nv[i] == j) tv[i] = t;
-                            }
-                        }
-                    }
-                    float v[V];
-#pragma unroll
-                    for (int i = 0; i < V; ++i) v[i] = unv[i] ? __fmul_rn(tv[i], wv[i]) : 0.0f;
-
-                    const float q = unit24(x.x);
-                    int kpick;
-                    if (q < A.q0) {
-                        // exploitation: argmax of tau*eta^beta, ties -> lowest rank.
-                        // Non-negative floats order like their bit patterns.
-                        uint32_t mb = 0u;
-#pragma unroll
-                        for (int i = 0; i < V; ++i)
-                            if (unv[i]) mb = max(mb, __float_as_uint(v[i]));
-#pragma unroll
-                        for (int off = TPA / 2; off >= 1; off >>= 1)
-                            mb = max(mb, __shfl_xor_sync(gmask, mb, off, TPA));
-                        int first = -1;
-#pragma unroll
-                        for (int i = V - 1; i >= 0; --i)
-                            if (unv[i] && __float_as_uint(v[i]) == mb) first = i;
-                        const unsigned bf = __ballot_sync(gmask, first >= 0) & gmask;
-                        const int src = __ffs(bf) - 1 - gbase;
-                        kpick = src * V + __shfl_sync(gmask, first, src, TPA);
-                    } else {
-                        // exploration: roulette of Eq. 2 over a 32-position
-                        // inclusive Hillis-Steele scan (offsets 1,2,4,8,16)
-                        const float r = unit24(x.y);
-                        float P[V];
-#pragma unroll
-                        for (int i = 0; i < V; ++i) P[i] = v[i];
-#pragma unroll
-                        for (int off = 1; off < 32; off <<= 1) {
-                            float y[V];
-                            if (off >= V) {
-                                const int dl = off / V;
-#pragma unroll
-                                for (int i = 0; i < V; ++i) {
-                                    const float o = __shfl_up_sync(gmask, P[i], dl, TPA);
-                                    y[i] = gl >= dl ? __fadd_rn(P[i], o) : P[i];
-                                }
-                            } else {
-                                float prev[V];
-#pragma unroll
-                                for (int i = 0; i < V; ++i) {
-                                    // positions i < off read the previous lane's V-off+i
-                                    if (i < off) prev[i] = __shfl_up_sync(gmask, P[i - off + V], 1, TPA);
-                                }
-#pragma unroll
-                                for (int i = 0; i < V; ++i) {
-                                    if (i >= off) y[i] = __fadd_rn(P[i], P[i - off]);
-                                    else y[i] = gl >= 1 ? __fadd_rn(P[i], prev[i]) : P[i];
-                                }
-                            }
-#pragma unroll
-                            for (int i = 0; i < V; ++i) P[i] = y[i];
-                        }
-                        const float total = __shfl_sync(gmask, P[V - 1], TPA - 1, TPA);
-                        const float t = __fmul_rn(r, total);
-                        int first = -1, last = -1, firstu = -1;
-#pragma unroll
-                        for (int i = 0; i < V; ++i) {
-                            const bool pos = unv[i] && v[i] > 0.0f;
-                            if (first < 0 && pos && P[i] > t) first = i;
-                            if (pos) last = i;
-                            if (firstu < 0 && unv[i]) firstu = i;
-                        }
-                        const unsigned bf = __ballot_sync(gmask, first >= 0) & gmask;
-                        const unsigned bl = __ballot_sync(gmask, last >= 0) & gmask;
-                        const unsigned bu = __ballot_sync(gmask, firstu >= 0) & gmask;
-                        if (bf) {
-                            const int src = __ffs(bf) - 1 - gbase;
-                            kpick = src * V + __shfl_sync(gmask, first, src, TPA);
-                        } else if (bl) {
-                            const int src = 31 - __clz(bl) - gbase;
-                            kpick = src * V + __shfl_sync(gmask, last, src, TPA);
-                        } else {
-                            const int src = __ffs(bu) - 1 - gbase;
-                            kpick = src * V + __shfl_sync(gmask, firstu, src, TPA);
-                        }
-                    }
-                    // broadcast the chosen node and its pheromone from the owning lane
-                    const int owner = kpick / V, ii = kpick - owner * V;
-                    int myn = nv[0];
-#pragma unroll
-                    for (int i = 1; i < V; ++i)
-                        if (ii == i) myn = nv[i];
-                    const int next = __shfl_sync(gmask, myn, owner, TPA);
-                    if (gl == 0) {
-                        s_nxt[al] = next;
-                        pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
-                        tours[(size_t)a * n + step] = next;
-                        vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
-                    }
-                };
-                if (ml <= ngroups) {
-                    // at most one ant per group: the queue is published by a CTA
-                    // barrier between the two halves, so that warps without a
-                    // selection to make start the full scans at once
-                    const int al = group;
-                    int c = 0, nv[V];
-                    float wv[V];
-                    bool unv[V];
-                    uint4 x;
-                    bool busy = false;
-                    if (al < ml) busy = stage(al, c, nv, wv, unv, x);
-                    __syncthreads();   // the step's queue is complete
-                    if (busy) choose(al, c, nv, wv, unv, x);
+                // Phase A: pseudo-random-proportional rule on the candidate list
+                if (split) {
+                    // staged, and the queue published by a CTA barrier, during the
+                    // cluster barrier that ended the previous step: warps without
+                    // a selection to make start the full scans at once
+                    if (st_busy) choose(step, group, st_c, st_nv, st_wv, st_unv, st_x);
                 } else {
                     for (int al = group; al < ml; al += ngroups) {
                         int c = 0, nv[V];
                         float wv[V];
                         bool unv[V];
                         uint4 x;
-                        if (stage(al, c, nv, wv, unv, x)) choose(al, c, nv, wv, unv, x);
+                        if (stage(step, al, c, nv, wv, unv, x)) choose(step, al, c, nv, wv, unv, x);
                     }
                     __syncthreads();   // the step's queue is complete
                 }
@@ -594,7 +615,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                             atomicExch(A.status, 4);
                             next = c;
                         }
-                        s_nxt[al] = next;
+                        nodeb[step & 1][al] = next;
                         tours[(size_t)(a0 + al) * n + step] = next;
                         vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
                         pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
@@ -604,8 +625,8 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
             } else {
                 // closing edges (step n): last node back to the first
                 for (int al = tid; al < ml; al += nthr) {
-                    const int c = s_cur[al], next = s_start[al];
-                    s_nxt[al] = next;
+                    const int c = nodeb[(step - 1) & 1][al], next = s_start[al];
+                    nodeb[step & 1][al] = next;
                     pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
                 }
             }
@@ -745,14 +766,18 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     }
                 }
             }
-            for (int al = tid; al < ml; al += nthr) s_cur[al] = s_nxt[al];
-            // the queue counter of the next step was last read before the
-            // previous barrier, so it can be cleared now
-            if (tid == 0) {
-                misc->qn[(step + 1) & 1] = 0;
-                misc->work = 0;
+            if (tid == 0) misc->work = 0;   // phase B's claims ended before the barrier
+            cluster_arrive();
+            // the next step's candidate row, visited bits and draw (static data and
+            // this CTA's own state) are staged, and its queue published, while the
+            // cluster barrier completes
+            if (split) {
+                st_busy = false;
+                if (step + 1 < n && group < ml)
+                    st_busy = stage(step + 1, group, st_c, st_nv, st_wv, st_unv, st_x);
+                __syncthreads();
             }
-            cluster.sync();
+            cluster_wait();
         }
 
         // ---- tour lengths (Alg. 1 select_best), one group per ant
