@@ -14,6 +14,10 @@ Beside it, the JSON line carries the second half of the metric: the mean
 tour-length gap at equal GPU time of the learned prior against plain ACS on
 held-out n=2392 and n=5000 instances (gap_leg; --no-gap skips it).
 
+--workload selects another configuration (n198: one n=198 instance, m=32;
+batch256: 256 instances of uneven n, m=64; large16: 8 x n=10000 and
+8 x n=20000, m=256); the default is the paper-scale workload above.
+
 --impl reference times the CPU oracle (single thread) on a bounded sample of
 the same workload: each step is one oracle iteration of one of the four
 colonies in rotation.
@@ -31,35 +35,86 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SIZES = [1002, 2392]
-M = 128
 CL = 32
 MEM_NAMES = {0: "matrix", 1: "spm"}
 HBM_PEAK_FALLBACK = 6800.0
 
+# Workloads (synthetic stand-ins for the paper's TSPLIB instances). The default
+# is the paper-scale configuration; the others are the single-instance, batched
+# and large-scale configurations, selectable with --workload.
+WORKLOADS = {
+    "paper": {
+        "desc": "plain ACS at paper scale: n=1002 and n=2392 clustered (20 clusters, "
+                "sigma=300, [0,10000]^2, EUC_2D), m=128, 32-NN, beta=2, q0=0.9, "
+                "rho=xi=0.1, FP32 matrix and SPM s=8 (4 colonies)",
+        "m": 128, "memories": (0, 1),
+    },
+    "n198": {
+        "desc": "plain ACS on one instance: n=198 uniform in [0,10000]^2, EUC_2D, m=32, "
+                "32-NN, beta=2, q0=0.9, rho=xi=0.1, FP32 matrix",
+        "m": 32, "memories": (0,),
+    },
+    "batch256": {
+        "desc": "batched plain ACS: 256 instances, n uniform in [100,2500], even uniform / "
+                "odd clustered in [0,10000]^2, m=64, 32-NN, FP32 matrix and SPM s=8, one "
+                "launch per iteration for each memory",
+        "m": 64, "memories": (0, 1),
+    },
+    "large16": {
+        "desc": "large scale: 8 instances n=10000 and 8 instances n=20000, uniform in "
+                "[0,100000]^2, m=256, 32-NN, FP32 matrix and SPM s=8, one launch per "
+                "iteration for each memory",
+        "m": 256, "memories": (0, 1),
+    },
+}
+WORKLOAD = "paper"
+M = WORKLOADS[WORKLOAD]["m"]
+SIZES = [1002, 2392]
+
+
+def make_coords(seed_offset=0):
+    """Coordinates of the current workload's instances, one array each."""
+    from paper_1605_02669_gb300 import instances
+
+    if WORKLOAD == "paper":
+        return [instances.clustered(n, seed=2 + seed_offset) for n in (1002, 2392)]
+    if WORKLOAD == "n198":
+        return [instances.uniform(198, side=10000, seed=1 + seed_offset)]
+    if WORKLOAD == "batch256":
+        xy, off, _, _ = instances.mixed_batch(256, 100, 2500, seed=3 + seed_offset)
+        return [xy[off[b]:off[b + 1]] for b in range(256)]
+    if WORKLOAD == "large16":
+        return ([instances.uniform(10000, side=100000, seed=40 + i + seed_offset) for i in range(8)]
+                + [instances.uniform(20000, side=100000, seed=60 + i + seed_offset)
+                   for i in range(8)])
+    raise ValueError(WORKLOAD)
+
+
+def select_workload(name):
+    global WORKLOAD, M, SIZES
+    WORKLOAD = name
+    M = WORKLOADS[name]["m"]
+    SIZES = [c.shape[0] for c in make_coords()]
+
 
 def workload_config():
+    mems = WORKLOADS[WORKLOAD]["memories"]
+    ncol = len(SIZES) * len(mems)
     return {
-        "workload": "plain ACS at paper scale: n=1002 and n=2392 clustered (20 clusters, "
-                    "sigma=300, [0,10000]^2, EUC_2D), m=128, 32-NN, beta=2, q0=0.9, "
-                    "rho=xi=0.1, FP32 matrix and SPM s=8 (4 colonies)",
-        "instances": SIZES,
+        "workload": WORKLOADS[WORKLOAD]["desc"],
+        "name": WORKLOAD,
+        "instances": SIZES if len(SIZES) <= 16 else "%d instances, n in [%d, %d], sum %d"
+                     % (len(SIZES), min(SIZES), max(SIZES), sum(SIZES)),
         "m": M,
         "cl": CL,
-        "memories": ["matrix", "spm_s8"],
-        "step": "one ACS iteration of all 4 colonies",
+        "memories": [{0: "matrix", 1: "spm_s8"}[mm] for mm in mems],
+        "step": "one ACS iteration of all %d colonies" % ncol,
         "l2": "flushed between timed steps (256 MiB write)",
     }
 
 
-def make_coords(seed_offset=0):
-    from paper_1605_02669_gb300 import instances
-
-    return [instances.clustered(n, seed=2 + seed_offset) for n in SIZES]
-
-
 def ant_steps_per_iter():
-    return 2 * sum(M * (n - 1) for n in SIZES)
+    return len(WORKLOADS[WORKLOAD]["memories"]) * sum(M * (n - 1) for n in SIZES)
 
 
 def measured_peaks():
@@ -172,24 +227,25 @@ def run_reference(args, rank, world):
         return None
     coords = make_coords()
     colonies = []
-    for mem in (0, 1):
-        for xy in coords:
+    for mem in WORKLOADS[WORKLOAD]["memories"]:
+        for xy in coords[:4]:
             p = oracle.make_params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem,
                                    spm_slots=8, seed=1)
             colonies.append(oracle.Colony(xy, p))
+    k = len(colonies)
     units = [M * (c.n - 1) for c in colonies]
     for i in range(args.warmup):
-        colonies[i % 4].run(1)
+        colonies[i % k].run(1)
     t_total, u_total = 0.0, 0
     for i in range(args.steps):
-        c = colonies[i % 4]
+        c = colonies[i % k]
         t0 = time.perf_counter()
         c.run(1)
         t_total += time.perf_counter() - t0
-        u_total += units[i % 4]
+        u_total += units[i % k]
     value = u_total / t_total
-    sample = ("one single-thread oracle iteration per step, rotating over the 4 colonies "
-              "(n=1002/2392 x matrix/SPM, m=128)")
+    sample = ("one single-thread oracle iteration per step, rotating over %d colonies of the "
+              "workload (m=%d)" % (k, M))
     return {
         "impl": "reference",
         "metric": "ant-steps/s in tour construction",
@@ -217,24 +273,22 @@ def cpu_baseline_leg(seconds_budget=15.0):
     import oracle
 
     coords = make_coords()
-    done_units, t_total = 0, 0.0
-    iters = {}
-    for mem in (0, 1):
+    done_units, t_total, ran = 0, 0.0, 0
+    for mem in WORKLOADS[WORKLOAD]["memories"]:
         for xy in coords:
+            if t_total > seconds_budget:
+                break
             p = oracle.make_params(m=M, cl=CL, q0=0.9, memory=mem, spm_slots=8, seed=1)
             c = oracle.Colony(xy, p)
             t0 = time.perf_counter()
             c.run(1)
-            dt = time.perf_counter() - t0
-            t_total += dt
+            t_total += time.perf_counter() - t0
             done_units += M * (xy.shape[0] - 1)
-            iters["%s_n%d" % (MEM_NAMES[mem], xy.shape[0])] = 1
+            ran += 1
             c.close()
-            if t_total > seconds_budget:
-                break
     return {"value": done_units / t_total, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "one oracle iteration of each colony (n=1002/2392 x matrix/SPM, "
-                      "m=128), single thread, %.1f s" % t_total}
+            "sample": "one oracle iteration of each of %d colonies of the workload (m=%d), "
+                      "single thread, %.1f s" % (ran, M, t_total)}
 
 
 KERNEL_SOURCES = ["acs_construct.cu", "acs_device.cuh", "acs_internal.cuh"]
@@ -242,8 +296,8 @@ KERNEL_SOURCES = ["acs_construct.cu", "acs_device.cuh", "acs_internal.cuh"]
 # ncu capture each (profiles/), keyed by (memory, threads per ant, cluster
 # size) and valid only for the kernel sources they were taken on.
 CAPTURED_TRAFFIC = {
-    ("matrix", 32, 16): {"bytes": 36976128 + 370432, "sources": "e541c7890bd7"},
-    ("spm", 32, 16): {"bytes": 16452096 + 0, "sources": "e541c7890bd7"},
+    ("paper", "matrix", 32, 16): {"bytes": 36976128 + 370432, "sources": "e541c7890bd7"},
+    ("paper", "spm", 32, 16): {"bytes": 16452096 + 0, "sources": "e541c7890bd7"},
 }
 
 
@@ -258,7 +312,7 @@ def kernel_sources_digest():
 
 
 def kernel_traffic(memory, tpa, csize):
-    rec = CAPTURED_TRAFFIC.get((memory, tpa, csize))
+    rec = CAPTURED_TRAFFIC.get((WORKLOAD, memory, tpa, csize))
     if rec is None or rec["sources"] != kernel_sources_digest():
         return None
     return rec["bytes"]
@@ -270,15 +324,15 @@ def algorithmic_bytes(n, m, fallbacks, spm):
     pheromone of the candidates (matrix gather 128 B, or the SPM record
     s*8+4 = 68 B), the local update (matrix: 2 entries written, 8 B read+write
     of one edge = 16 B; SPM: two record read-modify-writes, 2*68 B); each
-    fallback selection reads the pheromone row (4n B, or the record) and the
-    coordinates (8n B)."""
+    fallback selection reads the heuristic row (4n B) and the pheromone row
+    (matrix, 4n B) or the record (SPM, 68 B)."""
     steps = m * (n - 1)
     if spm:
         per = 256 + 68 + 136
-        fb = fallbacks * (8 * n + 68)
+        fb = fallbacks * (4 * n + 68)
     else:
         per = 256 + 128 + 16
-        fb = fallbacks * 12 * n
+        fb = fallbacks * 8 * n
     return steps * per + fb
 
 
@@ -371,7 +425,7 @@ def run_ours(args, rank, world, local):
     sB = torch.cuda.Stream()
     ctxs = []
     tuning = {}
-    mems = {"both": (acs.ACS_MEM_MATRIX, acs.ACS_MEM_SPM), "matrix": (acs.ACS_MEM_MATRIX,),
+    mems = {"both": WORKLOADS[WORKLOAD]["memories"], "matrix": (acs.ACS_MEM_MATRIX,),
             "spm": (acs.ACS_MEM_SPM,)}[args.only]
     for mem, st in zip(mems, (sA, sB)):
         p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
@@ -461,8 +515,8 @@ def run_ours(args, rank, world, local):
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": kernel_traffic(name, t["threads_per_ant"], t["cluster_size"]),
-            "kernel": "construct_kernel<%d,%d> (%s, n=1002+2392 in one launch, clusters of %d)"
-                      % (t["threads_per_ant"], col.kernel_mode, name,
+            "kernel": "construct_kernel<%d,%d> (%s, %d instances in one launch, clusters of %d)"
+                      % (t["threads_per_ant"], col.kernel_mode, name, len(SIZES),
                          t["cluster_size"]),
             "peak_kind": peak_kind, "kernel_ms": 1000.0 * avg_s,
             "algorithmic_bytes_per_launch": bytes_launch,
@@ -477,7 +531,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cols = []
-        for mem in (acs.ACS_MEM_MATRIX, acs.ACS_MEM_SPM):
+        for mem in WORKLOADS[WORKLOAD]["memories"]:
             p = acs.params(m=M, cl=CL, memory=mem, spm_slots=8, seed=1)
             cols.append(acs.Colony(xy, p, offsets=off))
         d2h = 0
@@ -500,7 +554,7 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return None
-    gap = None if args.no_gap else gap_leg(args.gap_iters)
+    gap = None if (args.no_gap or WORKLOAD != "paper") else gap_leg(args.gap_iters)
     cpu = None if args.no_cpu_baseline else cpu_baseline_leg()
     return {
         "metric": "ant-steps/s in tour construction",
@@ -536,6 +590,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="paper",
+                    help="paper (default, the metric's configuration), n198, batch256, large16")
     ap.add_argument("--only", choices=["both", "matrix", "spm"], default="both",
                     help="time only one memory kind (profiling runs; the metric needs both)")
     ap.add_argument("--no-gap", action="store_true",
@@ -545,6 +601,7 @@ def main():
     ap.add_argument("--tpa", type=int, default=0, help="pin lanes per ant instead of autotuning")
     ap.add_argument("--cluster", type=int, default=0, help="pin the cluster size instead of autotuning")
     args = ap.parse_args()
+    select_workload(args.workload)
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
