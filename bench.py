@@ -442,7 +442,8 @@ def run_ours(args, rank, world, local):
             # restored afterwards, so the timed iterations are unaffected
             col.autotune(trial_iters=2)
         tuning[MEM_NAMES[mem]] = {"threads_per_ant": col.threads_per_ant,
-                                  "cluster_size": col.cluster_size}
+                                  "cluster_size": col.cluster_size,
+                                  "kernel_mode": col.kernel_mode}
         ctxs.append((col, st))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 

@@ -115,13 +115,21 @@ int32_t acs_threads_per_ant(const acs_ctx* ctx);
 acs_status acs_set_cluster_size(acs_ctx* ctx, int32_t csize);
 int32_t acs_cluster_size(const acs_ctx* ctx);
 
+/* SPM contexts (Sec. 3.2): 1 keeps record r in the shared memory of CTA
+ * r mod csize for each launch when the records fit (the default), 0 keeps
+ * the records in global memory (smaller CTAs, more of them per SM). Only
+ * speed depends on it: results are bit-identical. ACS_EINVAL if the value
+ * cannot launch (the previous setting is kept). No effect on the matrix. */
+acs_status acs_set_spm_resident(acs_ctx* ctx, int32_t resident);
+
 /* Variant of the construct kernel the context launches (no counterpart in the
  * paper; for profiling): 0 = pheromone matrix, 1 = SPM records in global
  * memory, 2 = SPM records resident in the shared memory of the cluster for
  * the launch. -1 for NULL. */
 int32_t acs_kernel_mode(const acs_ctx* ctx);
 
-/* Autotuner: for every (threads per ant, cluster size) pair that can launch,
+/* Autotuner: for every (threads per ant, cluster size) pair that can launch
+ * (and, on the SPM, both record placements of acs_set_spm_resident),
  * times `trial_iters` iterations after one warm-up iteration, restoring the
  * full colony state after every trial, and keeps the fastest pair (written to
  * *chosen_tpa / *chosen_csize when not NULL). Results and the iteration count

@@ -87,6 +87,8 @@ def load():
     L.acs_set_cluster_size.argtypes = [_vp, _i32]
     L.acs_cluster_size.argtypes = [_vp]
     L.acs_cluster_size.restype = _i32
+    L.acs_set_spm_resident.argtypes = [_vp, _i32]
+    L.acs_set_spm_resident.restype = ctypes.c_int
     L.acs_kernel_mode.argtypes = [_vp]
     L.acs_kernel_mode.restype = _i32
     L.acs_prior_features.argtypes = [_vp, _i32, _vp, _vp]
@@ -230,6 +232,10 @@ def acs_cluster_size(ctx):
     return int(load().acs_cluster_size(ctx))
 
 
+def acs_set_spm_resident(ctx, resident):
+    _check(load().acs_set_spm_resident(ctx, int(resident)), "acs_set_spm_resident")
+
+
 def acs_kernel_mode(ctx):
     return int(load().acs_kernel_mode(ctx))
 
@@ -342,6 +348,9 @@ class Colony:
     @property
     def cluster_size(self):
         return acs_cluster_size(self.ctx)
+
+    def set_spm_resident(self, resident):
+        acs_set_spm_resident(self.ctx, resident)
 
     @property
     def kernel_mode(self):

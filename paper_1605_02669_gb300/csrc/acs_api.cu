@@ -195,6 +195,7 @@ struct acs_ctx {
     ConstructArgs args{};
     int tpa = 8, grid = 1, block = 256, sms = 1, csize = 1, max_smem = 0, mode = 0;
     bool vis_smem = true, xy_smem = false;
+    bool spm_resident = true;   // SPM records in shared memory when they fit
     size_t smem = 0;
     int64_t iteration = 0;
     bool poisoned = false;
@@ -276,7 +277,8 @@ cudaError_t configure(acs_ctx* c, int tpa, int csize)
     int nrec = 0;
     if (spm) {
         const int want = (c->max_n + csize - 1) / csize;
-        if (smem_layout(m, mc, want, c->s, W, c->max_n, false, false).total <= lim) nrec = want;
+        if (c->spm_resident && smem_layout(m, mc, want, c->s, W, c->max_n, false, false).total <= lim)
+            nrec = want;
     }
     const int s = c->s;
     const SmemLayout base = smem_layout(m, mc, nrec, s, W, c->max_n, false, false);
@@ -669,6 +671,23 @@ acs_status acs_set_threads_per_ant(acs_ctx* c, int32_t tpa)
 
 int32_t acs_threads_per_ant(const acs_ctx* c) { return c ? c->tpa : -1; }
 
+acs_status acs_set_spm_resident(acs_ctx* c, int32_t resident)
+{
+    if (!c || (resident != 0 && resident != 1)) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    const bool old = c->spm_resident;
+    c->spm_resident = resident != 0;
+    cudaError_t e = configure(c, c->tpa, c->csize);
+    if (e == cudaErrorInvalidConfiguration) {
+        cudaGetLastError();
+        c->spm_resident = old;
+        configure(c, c->tpa, c->csize);
+        return ACS_EINVAL;
+    }
+    return fail_cuda(c, e);
+}
+
 acs_status acs_set_cluster_size(acs_ctx* c, int32_t csize)
 {
     if (!c || (csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16)) return ACS_EINVAL;
@@ -727,16 +746,23 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
     if (st == ACS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail_cuda(c, cudaErrorUnknown);
     const int64_t iter0 = c->iteration;
     int best_tpa = c->tpa, best_cs = c->csize;
+    bool best_res = c->spm_resident;
     float best_ms = 0.0f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == ACS_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail_cuda(c, cudaErrorUnknown);
     const int tpas[4] = {4, 8, 16, 32};
     const int css[5] = {1, 2, 4, 8, 16};
+    // SPM: records resident in shared memory, or in global memory (smaller
+    // CTAs, more of them per SM)
+    const int nres = c->p.memory == ACS_MEM_SPM ? 2 : 1;
+    for (int ri = 0; ri < nres && st == ACS_OK; ++ri)
     for (int ci = 0; ci < 5 && st == ACS_OK; ++ci) {
         for (int ti = 0; ti < 4 && st == ACS_OK; ++ti) {
             if (css[ci] > c->m) continue;
+            c->spm_resident = ri == 0;
             if (configure(c, tpas[ti], css[ci]) != cudaSuccess) { cudaGetLastError(); continue; }
+            if (ri == 1 && c->mode != 1) continue;   // nothing new to try
             st = acs_run_iterations(c, 1);  // warm-up, captures the graph
             if (st != ACS_OK) break;
             cudaEventRecord(e0, c->stream);
@@ -746,7 +772,12 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
             if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail_cuda(c, cudaErrorUnknown); break; }
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best_tpa = tpas[ti]; best_cs = css[ci]; }
+            if (best_ms == 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best_tpa = tpas[ti];
+                best_cs = css[ci];
+                best_res = c->spm_resident;
+            }
             for (Buf& x : bufs)
                 if (cudaMemcpyAsync(x.p, x.save, x.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
                     st = fail_cuda(c, cudaErrorUnknown);
@@ -760,6 +791,7 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
     if (e1) cudaEventDestroy(e1);
     c->iteration = iter0;
     c->last_launches = 0;
+    c->spm_resident = best_res;
     if (st != ACS_OK) return st;
     if (configure(c, best_tpa, best_cs) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
     if (chosen_tpa) *chosen_tpa = best_tpa;

@@ -87,6 +87,10 @@ def test_null_context_calls(lib):
     assert lib.acs_run_iterations(None, 1) == acs.ACS_EINVAL
     assert lib.acs_best_tour(None, 0, None, None) == acs.ACS_EINVAL
     assert lib.acs_iteration(None) == -1
+    assert lib.acs_set_spm_resident(None, 1) == acs.ACS_EINVAL
+    assert lib.acs_set_cluster_size(None, 2) == acs.ACS_EINVAL
+    assert lib.acs_set_threads_per_ant(None, 8) == acs.ACS_EINVAL
+    assert lib.acs_autotune(None, 1, None, None) == acs.ACS_EINVAL
     lib.acs_destroy(None)
 
 

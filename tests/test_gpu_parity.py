@@ -213,6 +213,26 @@ def test_cluster_sizes_are_identical(oracle_mod, csize, memory):
     assert_same_state(gpu, ref, memory)
 
 
+@pytest.mark.parametrize("csize,tpa", [(1, 8), (4, 16), (16, 32)])
+def test_spm_records_in_global_memory(oracle_mod, csize, tpa):
+    # records kept in global memory instead of the cluster's shared memory
+    xy = instances.clustered(700, seed=16)
+    gpu, ref = _pair(xy, memory=1, m=96, cl=32, spm_slots=8, q0=0.8, seed=11)
+    gpu.set_spm_resident(0)
+    gpu.set_cluster_size(csize)
+    gpu.set_threads_per_ant(tpa)
+    assert gpu.kernel_mode == 1
+    for _ in range(2):
+        gpu.run(1)
+        ref.run(1)
+    assert_same_state(gpu, ref, 1)
+    gpu.set_spm_resident(1)
+    assert gpu.kernel_mode == 2
+    gpu.run(1)
+    ref.run(1)
+    assert_same_state(gpu, ref, 1)
+
+
 def test_uneven_ant_split_over_cluster(oracle_mod):
     # m not a multiple of the cluster size: the last CTA owns fewer ants
     xy = instances.uniform(260, seed=15)
