@@ -126,14 +126,14 @@ __device__ __forceinline__ unsigned long long pack_pj(float p, int j)
            (unsigned long long)(0xffffffffu - (uint32_t)j);
 }
 
+// Warp maximum of the packed keys: the largest high word (product bits) by a
+// hardware reduction, then the largest low word among the lanes that hold it.
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k)
 {
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, k, off);
-        k = o > k ? o : k;
-    }
-    return k;
+    const uint32_t hi = (uint32_t)(k >> 32), lo = (uint32_t)k;
+    const uint32_t mh = __reduce_max_sync(0xffffffffu, hi);
+    const uint32_t ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    return ((unsigned long long)mh << 32) | ml;
 }
 
 template <int V>
@@ -166,16 +166,18 @@ __device__ __forceinline__ void load_row(const int32_t* nrow, const float* wrow,
 
 }  // namespace
 
-// Total of `v` over the T consecutive lanes of this lane's segment.
-template <typename Tv>
-__device__ __forceinline__ Tv seg_sum(Tv v, int T)
+// Total of `v` over the T consecutive lanes of this lane's segment (a
+// hardware warp reduction when the segment is the whole warp).
+__device__ __forceinline__ int seg_sum(int v, int T)
 {
+    if (T == 32) return (int)__reduce_add_sync(0xffffffffu, (unsigned)v);
     for (int off = T / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, T);
     return v;
 }
 
 __device__ __forceinline__ int seg_min(int v, int T)
 {
+    if (T == 32) return __reduce_min_sync(0xffffffffu, v);
     for (int off = T / 2; off >= 1; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off, T));
     return v;
 }
