@@ -425,9 +425,13 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
 #pragma unroll
                 for (int i = 0; i < V; ++i)
                     if (unv[i]) mb = max(mb, __float_as_uint(v[i]));
+                if constexpr (TPA == 32) {
+                    mb = __reduce_max_sync(0xffffffffu, mb);
+                } else {
 #pragma unroll
-                for (int off = TPA / 2; off >= 1; off >>= 1)
-                    mb = max(mb, __shfl_xor_sync(gmask, mb, off, TPA));
+                    for (int off = TPA / 2; off >= 1; off >>= 1)
+                        mb = max(mb, __shfl_xor_sync(gmask, mb, off, TPA));
+                }
                 int first = -1;
 #pragma unroll
                 for (int i = V - 1; i >= 0; --i)
