@@ -528,7 +528,10 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
             int* qn = &misc->qn[step & 1];
             // the next step's queue counter was last read before the barrier
             // that ended phase B of the previous step
-            if (tid == 0) misc->qn[(step + 1) & 1] = 0;
+            if (tid == 0) {
+                misc->qn[(step + 1) & 1] = 0;
+                misc->nrel = 0;   // last read before the barrier that ended the previous step
+            }
 
             if (!closing) {
                 // Phase A: pseudo-random-proportional rule on the candidate list
@@ -649,34 +652,32 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                         t_own = __ldcg(tau + (size_t)(e >> 16) * n + (e & 0xffffu));
                     }
                 }
-                // every CTA gathers all m edges (one thread per ant: m <= nthr)
-                if (tid == 0) misc->nrel = 0;
-                if (tid < m) {
-                    const int a = tid;
-                    const int r = a / mc;
-                    const uint32_t e = cluster.map_shared_rank(pedge, r)[a - r * mc];
-                    const int u = (int)(e >> 16), v = (int)(e & 0xffffu);
-                    gkey[a] = (uint32_t)min(u, v) * (uint32_t)n + (uint32_t)max(u, v);
-                    gu[a] = u;
-                    gv[a] = v;
-                }
-                __syncthreads();
+                // every CTA gathers all m edges (one thread per ant: m <= nthr).
                 // This CTA only needs the edges it writes: on the matrix its own
                 // ants' edges, on the SPM the edges that touch one of its records
-                // (their events are the only ones replayed here).
-                if constexpr (SPM) {
-                    // compaction with one shared-memory atomic per warp
-                    if (tid < ((m + 31) & ~31)) {
-                        const int a = tid;
-                        const bool rel = a < m && ((gu[a] % C) == rank || (gv[a] % C) == rank);
+                // (their events are the only ones replayed here), compacted with
+                // one shared-memory atomic per warp.
+                if (tid < ((m + 31) & ~31)) {
+                    const int a = tid;
+                    bool rel = false;
+                    if (a < m) {
+                        const int r = a / mc;
+                        const uint32_t e = cluster.map_shared_rank(pedge, r)[a - r * mc];
+                        const int u = (int)(e >> 16), v = (int)(e & 0xffffu);
+                        gkey[a] = (uint32_t)min(u, v) * (uint32_t)n + (uint32_t)max(u, v);
+                        gu[a] = u;
+                        gv[a] = v;
+                        rel = (u % C) == rank || (v % C) == rank;
+                    }
+                    if constexpr (SPM) {
                         const unsigned bal = __ballot_sync(0xffffffffu, rel);
                         int base = 0;
                         if (lane == 0 && bal) base = atomicAdd(&misc->nrel, __popc(bal));
                         base = __shfl_sync(0xffffffffu, base, 0);
                         if (rel) eqal[base + __popc(bal & ((1u << lane) - 1u))] = a;
                     }
-                    __syncthreads();
                 }
+                __syncthreads();
                 const int NR = SPM ? misc->nrel : ml;
                 // k = ants on the same undirected edge, representative = lowest
                 // ant; T threads per relevant edge compare it with every T-th edge
