@@ -56,7 +56,6 @@ struct Misc {
     long long best_len;
     long long iteration;
     int nrel;                     // edges this CTA writes in the current step
-    int work;                     // next phase-B item to claim
 };
 
 __device__ __forceinline__ bool visited(const uint32_t* vis, int j)
@@ -311,7 +310,6 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         if (tid == 0) {
             misc->qn[0] = 0;
             misc->qn[1] = 0;
-            misc->work = 0;
             misc->best_len = __ldcg(A.best_len + b);
             misc->iteration = __ldcg(A.iteration + b);
             for (int i = 0; i < 4; ++i) misc->stat[i] = 0ull;
@@ -554,16 +552,17 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
 
                 // Phase B: the CTA's queued ants take the argmax of tau*eta^beta
                 // over all their unvisited nodes (Alg. 2, Sec. 3.1.1). The scan is
-                // cut into items of 128 nodes of one queued ant; warps claim items
-                // from a shared counter as soon as their selections are done.
+                // cut into items of 128 nodes of one queued ant, dealt round-robin
+                // to the warps that hold no ant of a split step (they start at
+                // once), or to every warp when there are none.
                 const int E = *qn;
                 const int nch = (n + 127) >> 7;
                 const int items = E * nch;
-                for (;;) {
-                    int item = 0;
-                    if (lane == 0) item = atomicAdd(&misc->work, 1);
-                    item = __shfl_sync(0xffffffffu, item, 0);
-                    if (item >= items) break;
+                const int nwarps = nthr >> 5, warp = tid >> 5;
+                const int antw = split ? (ml * TPA + 31) >> 5 : 0;   // warps holding ants
+                const int fw0 = antw < nwarps ? antw : 0;
+                const int nscan = nwarps - fw0;
+                for (int item = warp - fw0; warp >= fw0 && item < items; item += nscan) {
                     const int e = item / nch, ch = item - e * nch;
                     const int c = qc[e];
                     const uint32_t* vis = vis_base + (size_t)qant[e] * W;
@@ -573,16 +572,29 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     unsigned long long key = 0ull;
                     uint32_t word[4];
                     float t[4], h[4];
+                    // all loads of the item are issued before any is used
+                    const int jb = (ch << 7) + lane;
+                    if (hrow) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            h[i] = jb + i * 32 < n ? __ldg(hrow + jb + i * 32) : 0.0f;
+                    }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int j = (ch << 7) + i * 32 + lane;
-                        word[i] = 0xffffffffu;
+                        const int j = jb + i * 32;
                         t[i] = tau0;
-                        h[i] = 0.0f;
-                        if (j < n) {
-                            word[i] = vis[j >> 5];
-                            if constexpr (!SPM) t[i] = __ldcg(trow + j);
-                            h[i] = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
+                        if constexpr (!SPM) if (j < n) t[i] = __ldcg(trow + j);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int j = jb + i * 32;
+                        word[i] = j < n ? vis[j >> 5] : 0xffffffffu;
+                    }
+                    if (!hrow) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int j = jb + i * 32;
+                            h[i] = j < n ? heuristic(euc2d(pc, xy[j]), A.beta) : 0.0f;
                         }
                     }
 #pragma unroll
@@ -773,7 +785,6 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     }
                 }
             }
-            if (tid == 0) misc->work = 0;   // phase B's claims ended before the barrier
             cluster_arrive();
             // the next step's candidate row, visited bits and draw (static data and
             // this CTA's own state) are staged, and its queue published, while the
