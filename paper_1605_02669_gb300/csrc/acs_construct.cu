@@ -201,6 +201,12 @@ __device__ __forceinline__ void prefetch_l2(const void* p)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Bring the line holding p into this SM's L1 (read-only data only).
+__device__ __forceinline__ void prefetch_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // MODE 0: pheromone matrix. MODE 1: SPM records in global memory. MODE 2: SPM
 // record r resident, for the launch, in the shared memory of CTA r mod C
 // (loaded at the start, written back after the global update); other CTAs
@@ -363,10 +369,11 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                 qc[qi] = c;
                 qpart[qi] = 0ull;
             }
-            // phase B scans row c: stage it in L2
+            // phase B scans row c: stage the pheromone row in L2 and the heuristic
+            // row (read-only) in this SM's L1
             for (int j = gl * 32; j < n; j += TPA * 32) {
                 if constexpr (!SPM) prefetch_l2(tau + (size_t)c * n + j);
-                if (hw) prefetch_l2(hw + (size_t)c * n + j);
+                if (hw) prefetch_l1(hw + (size_t)c * n + j);
             }
             return false;
         };
@@ -572,6 +579,17 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     unsigned long long key = 0ull;
                     uint32_t word[4];
                     float t[4], h[4];
+                    // SPM: the record's own entries ride with the first item of
+                    // the ant (slot `lane`), loaded first so that they overlap
+                    int oj = -1;
+                    float ot = 0.0f;
+                    if constexpr (SPM) {
+                        if (ch == 0 && lane < s_slots) {
+                            const Rec R = rec(c);
+                            oj = ld_i<RG>(R.idx + lane);
+                            ot = ld_f<RG>(R.val + lane);
+                        }
+                    }
                     // all loads of the item are issued before any is used
                     const int jb = (ch << 7) + lane;
                     if (hrow) {
@@ -611,15 +629,10 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                         // the record's own entries are offered with their stored
                         // trails: the largest product and its lowest node are the
                         // same as with every trail read from the record.
-                        if (ch == 0 && lane < s_slots) {
-                            const Rec R = rec(c);
-                            const int j = ld_i<RG>(R.idx + lane);
-                            if (j >= 0 && !visited(vis, j)) {
-                                const float tr = ld_f<RG>(R.val + lane);
-                                const float hj = hrow ? hrow[j] : heuristic(euc2d(pc, xy[j]), A.beta);
-                                const unsigned long long k2 = pack_pj(__fmul_rn(tr, hj), j);
-                                key = k2 > key ? k2 : key;
-                            }
+                        if (oj >= 0 && !visited(vis, oj)) {
+                            const float hj = hrow ? __ldg(hrow + oj) : heuristic(euc2d(pc, xy[oj]), A.beta);
+                            const unsigned long long k2 = pack_pj(__fmul_rn(ot, hj), oj);
+                            key = k2 > key ? k2 : key;
                         }
                     }
                     key = warp_max_u64(key);
