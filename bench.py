@@ -415,6 +415,40 @@ def gap_leg(iters, log=None):
     }
 
 
+def relaxed_leg(xy, off, steps, warmup):
+    """The relaxed construction (ACS-GPU-Alt, Sec. 3.1.2) on the same instances,
+    pheromone matrix: no step barrier, racy local updates (not bit-exact),
+    evaluation and global update in a second kernel. Timed like the main line."""
+    import torch
+
+    from paper_1605_02669_gb300 import acs
+
+    st = torch.cuda.Stream()
+    col = acs.Colony(xy, acs.params(m=M, cl=CL, seed=1, relaxed=True), offsets=off)
+    col.set_stream(st.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        col.run(1)
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        col.run(1)
+        e1.record(st)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    units = sum(M * (n - 1) for n in SIZES) * steps
+    best = [int(col.best(b)[1]) for b in range(len(SIZES))]
+    col.close()
+    return {"value": units / (total / 1000.0), "unit": "ant-steps/s",
+            "ms_per_iteration": total / steps, "memory": "matrix", "best_len": best,
+            "note": "relaxed construction (ACS-GPU-Alt): racy local updates, not bit-exact; "
+                    "the synchronous deterministic kernels give the main value"}
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -564,6 +598,7 @@ def run_ours(args, rank, world, local):
     if rank != 0:
         return None
     gap = None if (args.no_gap or WORKLOAD != "paper") else gap_leg(args.gap_iters)
+    relaxed = None if args.no_relaxed else relaxed_leg(xy, off, args.steps, args.warmup)
     cpu = None if args.no_cpu_baseline else cpu_baseline_leg()
     return {
         "metric": "ant-steps/s in tour construction",
@@ -588,6 +623,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "tuning": tuning,
         "gap_at_equal_time": gap,
+        "relaxed": relaxed,
     }
 
 
@@ -605,6 +641,8 @@ def main():
                     help="time only one memory kind (profiling runs; the metric needs both)")
     ap.add_argument("--no-gap", action="store_true",
                     help="skip the learned-prior gap leg (profiling runs)")
+    ap.add_argument("--no-relaxed", action="store_true",
+                    help="skip the relaxed-construction leg")
     ap.add_argument("--gap-iters", type=int, default=1000,
                     help="iterations of the plain colony in the gap leg")
     ap.add_argument("--tpa", type=int, default=0, help="pin lanes per ant instead of autotuning")

@@ -72,9 +72,19 @@ typedef struct {
     int32_t  local_period; /* local update only at steps s with s % k == 0
                               (Sec. 4, "Limiting the number of local
                               pheromone updates"); 1 = every step */
-    int32_t  flags;        /* reserved, must be 0 */
+    int32_t  flags;        /* 0, or ACS_FLAG_RELAXED */
     uint64_t seed;         /* Philox key */
 } acs_params;
+
+/* ACS_FLAG_RELAXED: the relaxed construction of ACS-GPU-Alt (Sec. 3.1.2):
+ * every ant builds its whole tour in one pass with no step barrier and
+ * applies the local update to each edge at once with plain loads and stores,
+ * so concurrent updates may be lost and results depend on timing (tours stay
+ * valid; not bit-reproducible, no oracle parity). The evaluation and the
+ * global update follow in a second kernel. Pheromone matrix only (an SPM
+ * context with this flag is ACS_EINVAL). The autotuner has nothing to choose
+ * for it. */
+#define ACS_FLAG_RELAXED 1
 
 typedef struct acs_ctx acs_ctx;
 

@@ -8,7 +8,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libacs.so")
-SOURCES = ["acs_api.cu", "acs_construct.cu", "acs_noalloc.cu", "acs_prior.cu"]
+SOURCES = ["acs_api.cu", "acs_construct.cu", "acs_noalloc.cu", "acs_prior.cu", "acs_relaxed.cu"]
 HEADERS = ["acs_internal.cuh", "acs_device.cuh"]
 
 NVCC_FLAGS = [

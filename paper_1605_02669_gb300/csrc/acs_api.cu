@@ -21,6 +21,7 @@ cudaError_t prepare_construct(int tpa, int mode, size_t smem);
 cudaError_t launch_construct(const ConstructArgs& A, int tpa, int mode, int grid, int block,
                              size_t smem, int csize, cudaStream_t stream);
 int construct_occupancy(int tpa, int mode, int block, size_t smem, int csize);
+cudaError_t launch_relaxed(const ConstructArgs& A, int num_inst, int max_w, cudaStream_t stream);
 }  // namespace acs
 
 using namespace acs;
@@ -238,7 +239,8 @@ acs_status validate_params(const acs_params* p)
     if (!(p->xi > 0.0f && p->xi < 1.0f)) return ACS_EINVAL;
     if (p->memory != ACS_MEM_MATRIX && p->memory != ACS_MEM_SPM) return ACS_EINVAL;
     if (p->memory == ACS_MEM_SPM && (p->spm_slots < 1 || p->spm_slots > 32)) return ACS_EINVAL;
-    if (p->local_period < 1 || p->flags != 0) return ACS_EINVAL;
+    if (p->local_period < 1 || (p->flags & ~ACS_FLAG_RELAXED) != 0) return ACS_EINVAL;
+    if ((p->flags & ACS_FLAG_RELAXED) && p->memory != ACS_MEM_MATRIX) return ACS_EINVAL;
     return ACS_OK;
 }
 
@@ -639,8 +641,10 @@ acs_status acs_run_iterations(acs_ctx* c, int32_t iters)
     if (!c->exec) {
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return fail_cuda(c, e);
-        cudaError_t le = launch_construct(c->args, c->tpa, c->mode, c->grid, c->block, c->smem,
-                                          c->csize, c->stream);
+        cudaError_t le = (c->p.flags & ACS_FLAG_RELAXED)
+                             ? launch_relaxed(c->args, c->B, (c->max_n + 31) / 32, c->stream)
+                             : launch_construct(c->args, c->tpa, c->mode, c->grid, c->block,
+                                                c->smem, c->csize, c->stream);
         e = cudaStreamEndCapture(c->stream, &c->graph);
         if (le != cudaSuccess) return fail_cuda(c, le);
         if (e != cudaSuccess) return fail_cuda(c, e);
@@ -652,7 +656,7 @@ acs_status acs_run_iterations(acs_ctx* c, int32_t iters)
         if (e != cudaSuccess) return fail_cuda(c, e);
     }
     c->iteration += iters;
-    c->last_launches = iters;
+    c->last_launches = (c->p.flags & ACS_FLAG_RELAXED) ? 2ll * iters : iters;
     return ACS_OK;
 }
 
@@ -709,6 +713,11 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
 {
     if (!c || trial_iters < 1) return ACS_EINVAL;
     if (c->poisoned) return ACS_ESTATE;
+    if (c->p.flags & ACS_FLAG_RELAXED) {   // one launch shape only
+        if (chosen_tpa) *chosen_tpa = 32;
+        if (chosen_csize) *chosen_csize = 1;
+        return ACS_OK;
+    }
     // every mutable array of the context, restored after each trial
     struct Buf { void* p; size_t bytes; void* save; };
     size_t tau_n = 0, tour_n = 0, node_n = 0;

@@ -57,10 +57,19 @@ def _create_status(coords, p, n=None):
                                 dict(q0=-0.1), dict(q0=1.5), dict(rho=0.0), dict(rho=1.0),
                                 dict(xi=0.0), dict(beta=-1), dict(beta=9),
                                 dict(memory=3), dict(memory=1, spm_slots=0),
-                                dict(memory=1, spm_slots=33), dict(local_period=0)])
+                                dict(memory=1, spm_slots=33), dict(local_period=0),
+                                dict(memory=1, relaxed=True)])
 def test_bad_params_rejected_on_host(lib, kw):
     xy = instances.uniform(20, seed=1)
     rc, h = _create_status(xy, acs.params(**kw))
+    assert rc == acs.ACS_EINVAL and not h.value
+
+
+def test_unknown_flags_rejected_on_host(lib):
+    xy = instances.uniform(20, seed=1)
+    p = acs.params()
+    p.flags = 2
+    rc, h = _create_status(xy, p)
     assert rc == acs.ACS_EINVAL and not h.value
 
 
