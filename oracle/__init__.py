@@ -46,9 +46,13 @@ class Params(ctypes.Structure):
     ]
 
 
+FLAG_SPM_SKIP_DEFAULT = 2
+
+
 def make_params(m=32, cl=32, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=0,
-                spm_slots=8, local_period=1, seed=1):
-    return Params(m, cl, beta, q0, rho, xi, memory, spm_slots, local_period, 0, seed)
+                spm_slots=8, local_period=1, seed=1, spm_skip_default=False):
+    return Params(m, cl, beta, q0, rho, xi, memory, spm_slots, local_period,
+                  FLAG_SPM_SKIP_DEFAULT if spm_skip_default else 0, seed)
 
 
 _P = np.ctypeslib.ndpointer

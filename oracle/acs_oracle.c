@@ -61,7 +61,7 @@
 #define COORD_LIMIT (1 << 20)
 
 struct acsref_colony {
-    int32_t n, cl, m, beta, memory, s, period, instance;
+    int32_t n, cl, m, beta, memory, s, period, instance, flags;
     float q0, rho, xi, tau0;
     uint64_t seed;
     int32_t* xy;        /* 2n */
@@ -320,12 +320,22 @@ static void edge_update(acsref_colony* C, int32_t u, int32_t v, int32_t mode,
         C->tau[(size_t)v * C->n + u] = t2;
     } else {
         int32_t s = C->s;
-        acsref_spm_update(C->spm_idx + (size_t)u * s, C->spm_val + (size_t)u * s,
-                          C->spm_tail + u, s, v, C->tau0, mode, coef, target,
-                          &C->spm_hits, &C->spm_misses);
-        acsref_spm_update(C->spm_idx + (size_t)v * s, C->spm_val + (size_t)v * s,
-                          C->spm_tail + v, s, u, C->tau0, mode, coef, target,
-                          &C->spm_hits, &C->spm_misses);
+        for (int side = 0; side < 2; side++) {
+            const int32_t r = side ? v : u, nb = side ? u : v;
+            int32_t* idx = C->spm_idx + (size_t)r * s;
+            if (mode == 0 && (C->flags & ACSREF_FLAG_SPM_SKIP_DEFAULT)) {
+                /* variant: an absent edge keeps tau0 without an insert */
+                int present = 0;
+                for (int32_t i = 0; i < s; i++)
+                    if (idx[i] == nb) present = 1;
+                if (!present) {
+                    C->spm_misses++;
+                    continue;
+                }
+            }
+            acsref_spm_update(idx, C->spm_val + (size_t)r * s, C->spm_tail + r, s, nb,
+                              C->tau0, mode, coef, target, &C->spm_hits, &C->spm_misses);
+        }
     }
 }
 
@@ -340,7 +350,7 @@ static int validate(const int32_t* xy, int32_t n, const acsref_params* p)
     if (!(p->xi > 0.0f && p->xi < 1.0f)) return 1;
     if (p->memory != 0 && p->memory != 1) return 1;
     if (p->memory == 1 && (p->spm_slots < 1 || p->spm_slots > 32)) return 1;
-    if (p->local_period < 1 || p->flags != 0) return 1;
+    if (p->local_period < 1 || (p->flags & ~ACSREF_FLAG_SPM_SKIP_DEFAULT) != 0) return 1;
     for (int32_t i = 0; i < 2 * n; i++)
         if (xy[i] < 0 || xy[i] >= COORD_LIMIT) return 1;
     return 0;
@@ -354,7 +364,7 @@ static int colony_alloc(const int32_t* xy, int32_t n, int32_t cl,
     if (!C) return 2;
     C->n = n; C->cl = cl; C->m = p->m; C->beta = p->beta;
     C->memory = p->memory; C->s = p->memory == 1 ? p->spm_slots : 0;
-    C->period = p->local_period; C->instance = instance;
+    C->period = p->local_period; C->instance = instance; C->flags = p->flags;
     C->q0 = p->q0; C->rho = p->rho; C->xi = p->xi; C->seed = p->seed;
     size_t nn_sz = (size_t)n * cl;
     C->xy = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)n);

@@ -29,9 +29,14 @@ typedef struct {
     int32_t  memory;       /* 0 = n x n matrix, 1 = selective pheromone memory */
     int32_t  spm_slots;    /* s, slots per record, 1..32 */
     int32_t  local_period; /* local update on every k-th step, >= 1 */
-    int32_t  flags;        /* reserved, must be 0 */
+    int32_t  flags;        /* 0, or ACSREF_FLAG_SPM_SKIP_DEFAULT */
     uint64_t seed;         /* Philox key */
 } acsref_params;
+
+/* SPM variant: a local update (Eq. 3) of an edge absent from a record leaves
+ * the default value tau0, so it is not inserted (no eviction); it still
+ * counts as a miss. Alg. 3 as printed inserts it (the default, flag off). */
+#define ACSREF_FLAG_SPM_SKIP_DEFAULT 2
 
 typedef struct acsref_colony acsref_colony;
 

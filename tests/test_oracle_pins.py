@@ -413,6 +413,39 @@ def test_spm_small_memory_differs_and_counts(oracle_mod):
     assert misses > 0 and hits > 0
 
 
+def test_spm_skip_default_first_iteration_closed_form(oracle_mod):
+    # With the skip-default variant, every local update of the first iteration
+    # hits an absent edge (tau0 stays tau0) and inserts nothing; the global
+    # update then inserts the best tour's two neighbours of every node with
+    # the value tau0 + rho*(Delta - tau0). Each local event counts as a miss.
+    n, m = 30, 12
+    xy = instances.uniform(n, seed=17)
+    b = oracle.Colony(xy, oracle.make_params(m=m, cl=8, q0=0.6, memory=1, spm_slots=4,
+                                             spm_skip_default=True, seed=5))
+    b.run(1)
+    val, idx, tail = b.pheromone()
+    tour, L = b.best()
+    delta = np.float32(1.0 / float(L))
+    tau0 = np.float32(b.tau0)
+    want = np.float32(tau0 + np.float32(np.float32(0.1) * np.float32(delta - tau0)))
+    for i in range(n):
+        r = int(tour[i])
+        nbrs = {int(tour[i - 1]), int(tour[(i + 1) % n])}
+        got = {int(j) for j in idx[r] if j >= 0}
+        assert got == nbrs
+        assert all(val[r][q] == want for q in range(4) if idx[r][q] >= 0)
+    fb, steps, hits, misses = b.stats()
+    assert hits == 0
+    # the local events are the distinct edges of each step, two records each,
+    # plus the 2n misses of the global update
+    assert misses >= 2 * n and (misses - 2 * n) % 2 == 0
+    # the same colony without the variant inserts during construction
+    a = oracle.Colony(xy, oracle.make_params(m=m, cl=8, q0=0.6, memory=1, spm_slots=4, seed=5))
+    a.run(1)
+    va, ia, _ = a.pheromone()
+    assert not np.array_equal(ia, idx)
+
+
 def _brute_force_opt(D):
     n = D.shape[0]
     best = None
