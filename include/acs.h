@@ -86,6 +86,12 @@ typedef struct {
  * for it. */
 #define ACS_FLAG_RELAXED 1
 
+/* ACS_FLAG_SPM_SKIP_DEFAULT: SPM variant of Alg. 3's insert rule. A local
+ * update (Eq. 3) of an edge absent from a record yields exactly tau0; with
+ * this flag it is not inserted (no eviction), and it still counts as a miss.
+ * Off by default (the paper inserts it). No effect on the matrix. */
+#define ACS_FLAG_SPM_SKIP_DEFAULT 2
+
 typedef struct acs_ctx acs_ctx;
 
 /* One instance. coords: host int32 [n][2] (x, y). Instance index 0.

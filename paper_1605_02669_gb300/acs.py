@@ -38,12 +38,14 @@ class acs_params(ctypes.Structure):
 
 
 ACS_FLAG_RELAXED = 1
+ACS_FLAG_SPM_SKIP_DEFAULT = 2
 
 
 def params(m=32, cl=32, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=ACS_MEM_MATRIX,
-           spm_slots=8, local_period=1, seed=1, relaxed=False):
-    return acs_params(m, cl, beta, q0, rho, xi, memory, spm_slots, local_period,
-                      ACS_FLAG_RELAXED if relaxed else 0, seed)
+           spm_slots=8, local_period=1, seed=1, relaxed=False, spm_skip_default=False):
+    flags = (ACS_FLAG_RELAXED if relaxed else 0) | \
+            (ACS_FLAG_SPM_SKIP_DEFAULT if spm_skip_default else 0)
+    return acs_params(m, cl, beta, q0, rho, xi, memory, spm_slots, local_period, flags, seed)
 
 
 _lib = None

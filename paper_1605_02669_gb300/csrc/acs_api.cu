@@ -239,7 +239,9 @@ acs_status validate_params(const acs_params* p)
     if (!(p->xi > 0.0f && p->xi < 1.0f)) return ACS_EINVAL;
     if (p->memory != ACS_MEM_MATRIX && p->memory != ACS_MEM_SPM) return ACS_EINVAL;
     if (p->memory == ACS_MEM_SPM && (p->spm_slots < 1 || p->spm_slots > 32)) return ACS_EINVAL;
-    if (p->local_period < 1 || (p->flags & ~ACS_FLAG_RELAXED) != 0) return ACS_EINVAL;
+    if (p->local_period < 1 ||
+        (p->flags & ~(ACS_FLAG_RELAXED | ACS_FLAG_SPM_SKIP_DEFAULT)) != 0)
+        return ACS_EINVAL;
     if ((p->flags & ACS_FLAG_RELAXED) && p->memory != ACS_MEM_MATRIX) return ACS_EINVAL;
     return ACS_OK;
 }
@@ -383,6 +385,7 @@ cudaError_t plan_launch(acs_ctx* c)
     A.beta = c->p.beta;
     A.s = c->s;
     A.period = c->p.local_period;
+    A.skip_default = (c->p.flags & ACS_FLAG_SPM_SKIP_DEFAULT) ? 1 : 0;
     A.key0 = (uint32_t)(c->p.seed & 0xffffffffull);
     A.key1 = (uint32_t)(c->p.seed >> 32);
     A.max_n = c->max_n;

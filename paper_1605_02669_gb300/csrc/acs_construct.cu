@@ -89,9 +89,11 @@ struct Rec {
 
 // Alg. 3 on one record: a hit updates in place, a miss evicts the slot after
 // tail. mode 0 = local (coef = P[k]), 1 = global (coef = rho, target = Delta).
+// skip: a local update of an absent edge keeps tau0 and inserts nothing (the
+// variant of the insert rule; a miss all the same).
 template <bool GLOBAL>
 __device__ __forceinline__ bool spm_apply(const Rec& R, int s, int nb, float tau0, int mode,
-                                          float coef, float target)
+                                          float coef, float target, bool skip = false)
 {
     int hit = -1;
 #pragma unroll 8
@@ -102,6 +104,7 @@ __device__ __forceinline__ bool spm_apply(const Rec& R, int s, int nb, float tau
         R.val[hit] = mode == 0 ? local_rule(t, tau0, coef) : global_rule(t, target, coef);
         return true;
     }
+    if (skip && mode == 0) return false;
     int t = ld_i<GLOBAL>(R.tail) + 1;
     if (t == s) t = 0;
     *R.tail = t;
@@ -781,12 +784,12 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
                     }
                     for (int t = 0;; ++t) {
                         if (p0 && r0 == t) {
-                            const bool hit = spm_apply<RG>(rec(u), s_slots, v, tau0, 0, coef, 0.0f);
+                            const bool hit = spm_apply<RG>(rec(u), s_slots, v, tau0, 0, coef, 0.0f, A.skip_default);
                             if (hit) ++n_hit; else ++n_miss;
                             p0 = false;
                         }
                         if (p1 && r1 == t) {
-                            const bool hit = spm_apply<RG>(rec(v), s_slots, u, tau0, 0, coef, 0.0f);
+                            const bool hit = spm_apply<RG>(rec(v), s_slots, u, tau0, 0, coef, 0.0f, A.skip_default);
                             if (hit) ++n_hit; else ++n_miss;
                             p1 = false;
                         }

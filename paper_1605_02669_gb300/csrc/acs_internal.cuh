@@ -57,6 +57,7 @@ struct ConstructArgs {
     int32_t vis_in_smem, xy_in_smem, max_n;
     int32_t mc;               // ants per CTA of a cluster = ceil(m / cluster size)
     int32_t nrec;             // SPM records per CTA in shared memory (0 = global)
+    int32_t skip_default;     // SPM: a local update of an absent edge inserts nothing
 };
 
 // Shared-memory carve of the construct kernel; the same arithmetic runs on

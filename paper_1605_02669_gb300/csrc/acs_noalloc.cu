@@ -150,6 +150,7 @@ extern "C" acs_status acs_iterate_noalloc(const int32_t* dev_coords, int32_t n,
     A.beta = p->beta;
     A.s = 0;
     A.period = p->local_period;
+    A.skip_default = 0;
     A.key0 = (uint32_t)(p->seed & 0xffffffffull);
     A.key1 = (uint32_t)(p->seed >> 32);
     A.vis_in_smem = 0;

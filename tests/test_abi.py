@@ -68,7 +68,7 @@ def test_bad_params_rejected_on_host(lib, kw):
 def test_unknown_flags_rejected_on_host(lib):
     xy = instances.uniform(20, seed=1)
     p = acs.params()
-    p.flags = 2
+    p.flags = 4
     rc, h = _create_status(xy, p)
     assert rc == acs.ACS_EINVAL and not h.value
 

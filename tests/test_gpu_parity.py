@@ -233,6 +233,36 @@ def test_spm_records_in_global_memory(oracle_mod, csize, tpa):
     assert_same_state(gpu, ref, 1)
 
 
+@pytest.mark.parametrize("resident", [1, 0])
+def test_spm_skip_default_variant(oracle_mod, resident):
+    # the variant of the insert rule: absent edges keep tau0 without an insert
+    xy = instances.clustered(600, seed=18)
+    kw = dict(m=64, cl=32, q0=0.85, memory=1, spm_slots=4, seed=12)
+    gpu = acs.Colony(xy, acs.params(spm_skip_default=True, **kw))
+    gpu.set_spm_resident(resident)
+    ref = oracle.Colony(xy, oracle.make_params(spm_skip_default=True, **kw))
+    for _ in range(3):
+        gpu.run(1)
+        ref.run(1)
+        assert_same_state(gpu, ref, 1)
+    assert np.array_equal(np.asarray(gpu.stats(0)), np.asarray(ref.stats()))
+
+
+@pytest.mark.parametrize("slots", [1, 2, 4, 8, 16, 32])
+def test_spm_hit_ratio_sweep(oracle_mod, slots):
+    # the hit ratio of the SPM counters, bit-exact with the oracle, in [0, 1]
+    xy = instances.uniform(400, seed=19)
+    kw = dict(m=32, cl=32, q0=0.9, memory=1, spm_slots=slots, seed=13)
+    gpu = acs.Colony(xy, acs.params(**kw))
+    ref = oracle.Colony(xy, oracle.make_params(**kw))
+    gpu.run(3)
+    ref.run(3)
+    g = np.asarray(gpu.stats(0))
+    assert np.array_equal(g, np.asarray(ref.stats()))
+    hits, misses = int(g[2]), int(g[3])
+    assert 0 <= hits / (hits + misses) <= 1
+
+
 def test_uneven_ant_split_over_cluster(oracle_mod):
     # m not a multiple of the cluster size: the last CTA owns fewer ants
     xy = instances.uniform(260, seed=15)
