@@ -99,6 +99,8 @@ def lib():
         L.acsref_get_tours.argtypes = [_vp, _P(np.int32), _P(np.int64)]
         L.acsref_best.argtypes = [_vp, _P(np.int32), ctypes.POINTER(_i64)]
         L.acsref_best.restype = ctypes.c_int
+        L.acsref_offer_best.argtypes = [_vp, _P(np.int32)]
+        L.acsref_offer_best.restype = ctypes.c_int
         L.acsref_get_pheromone.argtypes = [_vp, _P(np.float32), _vp, _vp]
         L.acsref_get_setup.argtypes = [_vp, _P(np.int32), _P(np.float32),
                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i64),
@@ -221,6 +223,11 @@ class Colony:
         L = np.zeros(self.m, np.int64)
         lib().acsref_get_tours(self._h, t, L)
         return t, L
+
+    def offer_best(self, tour):
+        rc = lib().acsref_offer_best(self._h, np.ascontiguousarray(tour, np.int32))
+        if rc != 0:
+            raise OracleError("not a tour of this instance")
 
     def best(self):
         t = np.zeros(self.n, np.int32)

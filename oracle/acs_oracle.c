@@ -582,6 +582,29 @@ int acsref_best(const acsref_colony* C, int32_t* tour, int64_t* len)
     return 0;
 }
 
+int acsref_offer_best(acsref_colony* C, const int32_t* tour)
+{
+    if (!C || !tour) return 1;
+    const int32_t n = C->n;
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    if (!seen) return 1;
+    int ok = 1;
+    for (int32_t i = 0; i < n && ok; i++) {
+        if (tour[i] < 0 || tour[i] >= n || seen[tour[i]]) ok = 0;
+        else seen[tour[i]] = 1;
+    }
+    free(seen);
+    if (!ok) return 1;
+    int64_t L = 0;
+    for (int32_t i = 0; i < n; i++) L += acsref_dist(C->xy, tour[i], tour[(i + 1) % n]);
+    if (!C->has_best || L < C->best_len) {
+        memcpy(C->best, tour, sizeof(int32_t) * (size_t)n);
+        C->best_len = L;
+        C->has_best = 1;
+    }
+    return 0;
+}
+
 int acsref_get_pheromone(const acsref_colony* C, float* tau_or_val,
                          int32_t* spm_idx, int32_t* spm_tail)
 {

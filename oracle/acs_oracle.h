@@ -64,6 +64,10 @@ int     acsref_create_tables(const int32_t* xy, int32_t n, const int32_t* nn,
 int     acsref_run(acsref_colony* c, int32_t iters);
 int     acsref_get_tours(const acsref_colony* c, int32_t* tours, int64_t* lens);
 int     acsref_best(const acsref_colony* c, int32_t* tour, int64_t* len);
+/* Offer a tour from elsewhere (another colony: multi-colony exchange). It
+ * replaces the best-so-far only if it is a permutation and strictly shorter
+ * (Alg. 1's replacement rule); returns 0, or 1 for a bad tour. */
+int     acsref_offer_best(acsref_colony* c, const int32_t* tour);
 int     acsref_get_pheromone(const acsref_colony* c, float* tau_or_val,
                              int32_t* spm_idx, int32_t* spm_tail);
 int     acsref_get_setup(const acsref_colony* c, int32_t* nn, float* w,

@@ -446,6 +446,33 @@ def test_spm_skip_default_first_iteration_closed_form(oracle_mod):
     assert not np.array_equal(ia, idx)
 
 
+def test_offer_best_keeps_the_strictly_shorter_tour(oracle_mod):
+    xy = instances.uniform(9, seed=31)
+    D = _np_dist(xy)
+    c = oracle.Colony(xy, oracle.make_params(m=4, cl=8, q0=0.5, seed=3))
+    c.run(1)
+    tour, L = c.best()
+    # the brute-force optimum is never longer: offering it replaces the best
+    # unless it ties; a longer tour is refused; a non-permutation is an error
+    opt = _brute_force_opt(D)
+    best_perm = None
+    for perm in itertools.permutations(range(1, 9)):
+        t = (0,) + perm
+        if sum(D[t[i], t[(i + 1) % 9]] for i in range(9)) == opt:
+            best_perm = np.array(t, np.int32)
+            break
+    c.offer_best(best_perm)
+    t2, L2 = c.best()
+    assert L2 == opt
+    if opt < L:
+        assert np.array_equal(t2, best_perm)
+    worse = np.arange(9, dtype=np.int32)
+    c.offer_best(worse)
+    assert c.best()[1] == opt
+    with pytest.raises(oracle.OracleError):
+        c.offer_best(np.zeros(9, np.int32))
+
+
 def _brute_force_opt(D):
     n = D.shape[0]
     best = None
