@@ -157,6 +157,16 @@ acs_status acs_autotune(acs_ctx* ctx, int32_t trial_iters, int32_t* chosen_tpa,
 /* Best-so-far tour (n node indices, 0-based, starting at the ant's first
  * node, closing implicitly) and its length. ACS_ESTATE before the first
  * iteration. */
+/* Multi-colony exchange (the paper's related work, Sec. 2; no counterpart in
+ * its algorithms): offer `tour` (host int32 [n], a permutation of the
+ * instance's nodes) as the best-so-far of `instance`. Its length is computed
+ * on the device; it replaces the best-so-far only if strictly shorter, the
+ * replacement rule of Alg. 1, so the next global update deposits on it.
+ * len_out (optional) receives the offered tour's length. ACS_EINVAL if the
+ * tour is not a permutation. Works before the first iteration too. */
+acs_status acs_offer_best_tour(acs_ctx* ctx, int32_t instance, const int32_t* tour,
+                               int64_t* len_out);
+
 acs_status acs_best_tour(acs_ctx* ctx, int32_t instance, int32_t* tour_out,
                          int64_t* len_out);
 

@@ -93,6 +93,8 @@ def load():
     L.acs_set_cluster_size.argtypes = [_vp, _i32]
     L.acs_cluster_size.argtypes = [_vp]
     L.acs_cluster_size.restype = _i32
+    L.acs_offer_best_tour.argtypes = [_vp, _i32, _vp, _vp]
+    L.acs_offer_best_tour.restype = ctypes.c_int
     L.acs_set_spm_resident.argtypes = [_vp, _i32]
     L.acs_set_spm_resident.restype = ctypes.c_int
     L.acs_kernel_mode.argtypes = [_vp]
@@ -164,6 +166,13 @@ def acs_best_tour(ctx, instance, n):
     L = np.zeros(1, np.int64)
     _check(load().acs_best_tour(ctx, instance, _ptr(t), _ptr(L)), "acs_best_tour")
     return t, int(L[0])
+
+
+def acs_offer_best_tour(ctx, instance, tour):
+    tour = np.ascontiguousarray(tour, np.int32)
+    L = np.zeros(1, np.int64)
+    _check(load().acs_offer_best_tour(ctx, instance, _ptr(tour), _ptr(L)), "acs_offer_best_tour")
+    return int(L[0])
 
 
 def acs_get_tours(ctx, instance, m, n):
@@ -375,6 +384,9 @@ class Colony:
     @property
     def iteration(self):
         return acs_iteration(self.ctx)
+
+    def offer_best(self, tour, b=0):
+        return acs_offer_best_tour(self.ctx, b, tour)
 
     def best(self, b=0):
         return acs_best_tour(self.ctx, b, self.sizes[b])

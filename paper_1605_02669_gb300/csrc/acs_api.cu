@@ -68,6 +68,36 @@ __global__ void knn_kernel(const InstDesc* desc, const int32_t* xy, int32_t* nn,
 
 // Nearest-neighbour tour from node 0 (ties -> lowest index), one CTA per
 // instance; sets tau0 = (float)(1/((double)n * L_nn)).
+// Offer a tour (already checked to be a permutation) as the best-so-far of
+// instance b: its EUC_2D length is summed by one CTA and the tour replaces
+// the best-so-far only when strictly shorter (Alg. 1's rule).
+__global__ void offer_best_kernel(const InstDesc* desc, int b, const int32_t* xy,
+                                  const int32_t* tour, int32_t* best, int64_t* best_len,
+                                  int64_t* len_out)
+{
+    __shared__ long long part[32];
+    __shared__ int take;
+    const InstDesc D = desc[b];
+    const int n = D.n, tid = threadIdx.x;
+    const int2* p = reinterpret_cast<const int2*>(xy) + D.xy_off;
+    long long sum = 0;
+    for (int i = tid; i < n; i += blockDim.x) sum += euc2d(p[tour[i]], p[tour[i + 1 < n ? i + 1 : 0]]);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if ((tid & 31) == 0) part[tid >> 5] = sum;
+    __syncthreads();
+    if (tid == 0) {
+        long long L = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) L += part[w];
+        take = L < best_len[b];
+        if (take) best_len[b] = L;
+        *len_out = L;
+    }
+    __syncthreads();
+    if (take)
+        for (int i = tid; i < n; i += blockDim.x) best[D.node_off + i] = tour[i];
+}
+
 __global__ void nn_tour_kernel(InstDesc* desc, const int32_t* xy, int64_t* L_out)
 {
     extern __shared__ uint32_t vis[];
@@ -808,6 +838,41 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
     if (configure(c, best_tpa, best_cs) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
     if (chosen_tpa) *chosen_tpa = best_tpa;
     if (chosen_csize) *chosen_csize = best_cs;
+    return ACS_OK;
+}
+
+acs_status acs_offer_best_tour(acs_ctx* c, int32_t b, const int32_t* tour, int64_t* len_out)
+{
+    if (!c || !tour || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    const InstDesc& D = c->desc_h[b];
+    const int n = D.n;
+    std::vector<uint8_t> seen((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (tour[i] < 0 || tour[i] >= n || seen[tour[i]]) return ACS_EINVAL;
+        seen[tour[i]] = 1;
+    }
+    acs_status s = check_device_status(c);
+    if (s != ACS_OK) return s;
+    // scratch: the tour and the offered length, stream-ordered
+    void* scratch = nullptr;
+    const size_t bytes = sizeof(int64_t) + sizeof(int32_t) * (size_t)n;
+    cudaError_t e = cudaMallocAsync(&scratch, bytes, c->stream);
+    if (e != cudaSuccess) { cudaGetLastError(); return ACS_ENOMEM; }
+    int64_t* d_len = static_cast<int64_t*>(scratch);
+    int32_t* d_tour = reinterpret_cast<int32_t*>(d_len + 1);
+    e = cudaMemcpyAsync(d_tour, tour, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        offer_best_kernel<<<1, 1024, 0, c->stream>>>(c->d_desc, b, c->d_xy, d_tour, c->d_best,
+                                                     c->d_best_len, d_len);
+        e = cudaGetLastError();
+    }
+    int64_t L = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&L, d_len, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(scratch, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    if (len_out) *len_out = L;
     return ACS_OK;
 }
 
