@@ -206,6 +206,9 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=11)
     ap.add_argument("--out", default="prior_params.npy")
+    ap.add_argument("--apply-n", type=int, default=0,
+                    help="then score and prune a generated clustered instance of this size "
+                         "and run it for a few iterations (0: skip)")
     a = ap.parse_args(argv)
     from . import build
 
@@ -215,6 +218,13 @@ def main(argv=None):
                       a.seed, log=print)
     np.save(a.out, params.cpu().numpy())
     print("trained in %.1f s -> %s" % (time.time() - t0, a.out))
+    if a.apply_n:
+        xy = instances.clustered(a.apply_n, seed=a.seed + 1)
+        col = acs.Colony(xy, acs.params(m=128, cl=32, seed=a.seed))
+        apply(col, params, keep=16)
+        col.run(3)
+        print("prior-pruned colony, n=%d: best %d after 3 iterations" % (a.apply_n, col.best(0)[1]))
+        col.close()
 
 
 if __name__ == "__main__":
