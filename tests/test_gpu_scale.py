@@ -106,3 +106,32 @@ def test_large_n20000_batch_properties(oracle_mod):
             assert tau.min() >= tau0
             assert tau.max() <= np.float32(1.0 / bl) * (1 + 2.0 ** -22)
         gpu.close()
+
+
+@pytest.mark.parametrize("memory", [0, 1])
+def test_maximum_n_65536_properties(memory):
+    # the largest instance the library accepts (n = 65536, coordinates up to
+    # 2^20 - 1). The oracle's set-up alone takes most of an hour at this size,
+    # so the checks are those that hold at any size, plus the candidate lists
+    # of sampled nodes against a brute-force sort.
+    n = 65536
+    xy = instances.uniform(n, side=(1 << 20) - 1, seed=23)
+    gpu = acs.Colony(xy, acs.params(m=8, cl=32, memory=memory, spm_slots=8, seed=2))
+    gpu.run(2)
+    t, L = gpu.tours(0)
+    bt, bl = gpu.best(0)
+    _check_properties(xy, t, L, bt, bl)
+    nn, w, tau0, _ = gpu.setup(0)
+    rng = np.random.default_rng(0)
+    p = xy.astype(np.int64)
+    for i in rng.choice(n, 24, replace=False):
+        d = np.floor(np.sqrt(((p - p[i]) ** 2).sum(1).astype(np.float64)) + 0.5).astype(np.int64)
+        d[i] = np.iinfo(np.int64).max
+        order = np.lexsort((np.arange(n), d))[:32]
+        assert np.array_equal(nn[i], order)
+    if memory == 1:
+        val, idx, tail = gpu.pheromone(0)
+        live = idx >= 0
+        assert val[live].min() >= tau0
+        assert val[live].max() <= np.float32(1.0 / bl) * (1 + 2.0 ** -22)
+    gpu.close()
