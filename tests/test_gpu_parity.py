@@ -70,6 +70,19 @@ def test_config_n198_m32_every_iteration(oracle_mod, memory):
         assert_same_state(gpu, ref, memory)
 
 
+@pytest.mark.parametrize("memory", [0, 1])
+def test_config_n198_m32_200_iterations(oracle_mod, memory):
+    # the single-instance configuration over its full 200 iterations: the state
+    # stays bit-identical through long stagnation (ties, repeated best tours)
+    xy = instances.uniform(198, side=10000, seed=1)
+    gpu, ref = _pair(xy, memory=memory, m=32, cl=32, spm_slots=8, seed=1)
+    for _ in range(4):
+        gpu.run(50)
+        ref.run(50)
+        assert_same_state(gpu, ref, memory)
+    assert np.array_equal(np.asarray(gpu.stats(0)), np.asarray(ref.stats()))
+
+
 EDGE_CASES = [
     dict(n=3, m=1, cl=32),
     dict(n=4, m=3, cl=32, q0=0.0),
