@@ -98,54 +98,57 @@ __global__ void offer_best_kernel(const InstDesc* desc, int b, const int32_t* xy
         for (int i = tid; i < n; i += blockDim.x) best[D.node_off + i] = tour[i];
 }
 
-__global__ void nn_tour_kernel(InstDesc* desc, const int32_t* xy, int64_t* L_out)
+// Nearest-neighbour tour from node 0 (ties -> lowest index) and tau0 =
+// 1/(n*L_nn), one warp per instance. The candidate list of the current node
+// holds its cl nearest nodes in (distance, index) order, so while one of them
+// is unvisited the first such one is the nearest unvisited node; only when
+// all are visited does the warp scan every node.
+__global__ void nn_tour_kernel(InstDesc* desc, const int32_t* xy, const int32_t* nn,
+                               int64_t* L_out)
 {
     extern __shared__ uint32_t vis[];
-    __shared__ unsigned long long red[32];
-    __shared__ int s_cur;
     InstDesc* D = desc + blockIdx.x;
-    const int n = D->n;
+    const int n = D->n, cl = D->cl, lane = threadIdx.x;
     const int W = (n + 31) >> 5;
     const int2* p = reinterpret_cast<const int2*>(xy) + D->xy_off;
-    for (int i = threadIdx.x; i < W; i += blockDim.x) vis[i] = 0u;
-    __syncthreads();
-    if (threadIdx.x == 0) { vis[0] = 1u; s_cur = 0; }
-    __syncthreads();
+    const int32_t* rows = nn + 32 * D->row_off;
+    for (int i = lane; i < W; i += 32) vis[i] = 0u;
+    __syncwarp();
+    if (lane == 0) vis[0] = 1u;
+    __syncwarp();
     long long L = 0;
+    int cur = 0;
     for (int step = 1; step < n; ++step) {
-        const int cur = s_cur;
         const int2 pc = p[cur];
-        unsigned long long bk = ~0ull;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            if ((vis[j >> 5] >> (j & 31)) & 1u) continue;
-            const unsigned long long key = ((unsigned long long)euc2d(pc, p[j]) << 32) | (uint32_t)j;
-            bk = key < bk ? key : bk;
-        }
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, bk, off);
-            bk = o < bk ? o : bk;
-        }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bk;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : ~0ull;
+        const int j = lane < cl ? rows[(size_t)cur * 32 + lane] : -1;
+        const bool unv = j >= 0 && !((vis[j >> 5] >> (j & 31)) & 1u);
+        const unsigned bal = __ballot_sync(0xffffffffu, unv);
+        int nx;
+        if (bal) {
+            nx = __shfl_sync(0xffffffffu, j, __ffs(bal) - 1);
+        } else {
+            unsigned long long bk = ~0ull;
+            for (int q = lane; q < n; q += 32) {
+                if ((vis[q >> 5] >> (q & 31)) & 1u) continue;
+                const unsigned long long key = ((unsigned long long)euc2d(pc, p[q]) << 32) | (uint32_t)q;
+                bk = key < bk ? key : bk;
+            }
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) {
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
-                v = o < v ? o : v;
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, bk, off);
+                bk = o < bk ? o : bk;
             }
-            if (threadIdx.x == 0) {
-                const int nx = (int)(v & 0xffffffffull);
-                L += (long long)(v >> 32);
-                vis[nx >> 5] |= 1u << (nx & 31);
-                s_cur = nx;
-            }
+            nx = (int)(bk & 0xffffffffull);
         }
-        __syncthreads();
+        if (lane == 0) {
+            L += euc2d(pc, p[nx]);
+            vis[nx >> 5] |= 1u << (nx & 31);
+        }
+        __syncwarp();
+        cur = nx;
     }
-    if (threadIdx.x == 0) {
-        L += euc2d(p[s_cur], p[0]);
+    if (lane == 0) {
+        L += euc2d(p[cur], p[0]);
         L_out[blockIdx.x] = L;
         D->tau0 = __double2float_rn(1.0 / ((double)n * (double)L));
     }
@@ -518,7 +521,7 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     knn_kernel<<<kg, 256, 0, st>>>(c->d_desc, c->d_xy, c->d_nn, c->d_w, c->p.beta);
     ACS_TRY(cudaGetLastError());
     const size_t vis_bytes = sizeof(uint32_t) * ((c->max_n + 31) / 32);
-    nn_tour_kernel<<<B, 1024, vis_bytes, st>>>(c->d_desc, c->d_xy, c->d_Lnn);
+    nn_tour_kernel<<<B, 32, vis_bytes, st>>>(c->d_desc, c->d_xy, c->d_nn, c->d_Lnn);
     ACS_TRY(cudaGetLastError());
     dim3 ig(256, B);
     if (c->d_hw) {
