@@ -15,9 +15,11 @@
  * pheromone memory is either the n x n FP32 matrix or the selective
  * pheromone memory (Sec. 3.2, Alg. 3).
  *
- * Determinism contract: for a given (coordinates, parameters, seed,
- * instance index) every call sequence yields bit-identical tours, tour
- * lengths and pheromone state, equal to the CPU oracle shipped with the tests.
+ * Determinism contract (all modes but ACS_FLAG_RELAXED, which trades it for
+ * speed): for a given (coordinates, parameters, seed, instance index) every
+ * call sequence yields bit-identical tours, tour lengths and pheromone state,
+ * equal to the CPU oracle shipped with the tests, whatever the launch shape
+ * (threads per ant, cluster size, SPM record placement).
  * All ants of a step read the pheromone state left by the previous step; an
  * undirected edge taken by k ants in one step gets one local update with
  * factor (1-xi)^k (tau <- tau0 + P[k]*(tau - tau0), P[k] an FP32 table built
