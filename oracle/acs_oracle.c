@@ -19,7 +19,7 @@
  *   Sec. 3.2, Alg. 3  : selective pheromone memory (per-node circular buffer
  *                       of s (node, trail) slots; absent edges read tau_min).
  *
- * Readings of the paper fixed here (each is also listed in the design doc):
+ * Readings of the paper fixed here (where it is silent, garbled or ambiguous):
  *   - Synchronous steps (the ACS-GPU model of Sec. 3.1.2): every ant picks its
  *     step-s node from the pheromone state left by step s-1; then the local
  *     updates of step s are applied. An undirected edge taken by k ants in one
