@@ -11,9 +11,11 @@
  *
  * Network: x[8] -> h1 = relu(x W1 + b1)[64] -> h2 = relu(h1 W2 + b2)[64]
  *          -> z = h2 w3 + b3 -> p = sigmoid(z).
- * The two hidden layers run on the tensor cores (mma.sync m16n8k16) with
- * BF16 operands (features, W1, h1, W2) and FP32 accumulation; biases, h2,
- * w3 and the last layer stay FP32.
+ * The two hidden layers run on the tensor cores with BF16 operands
+ * (features, W1, h1, W2) and FP32 accumulation; biases, h2, w3 and the last
+ * layer stay FP32. Scoring (acs_mlp_forward) issues tcgen05.mma with the
+ * accumulators in tensor memory; training (acs_mlp_train_batch) uses
+ * mma.sync m16n8k16 fragments in registers.
  *
  * Parameters are one FP32 device vector of ACS_MLP_PARAMS floats:
  *   W1 [8][64] at 0, b1 [64] at 512, W2 [64][64] at 576 (W2[in][out]),
@@ -58,8 +60,10 @@ acs_status acs_prior_features(acs_ctx* ctx, int32_t instance, uint16_t* dev_feat
 acs_status acs_prior_count_best_edges(acs_ctx* ctx, int32_t instance, float* dev_count,
                                       void* stream);
 
-/* Scores p = sigmoid(z) of `rows` feature rows (dev_feat [rows][8] BF16)
- * into dev_p [rows] FP32. */
+/* Scores p = sigmoid(z) of `rows` feature rows (dev_feat [rows][8] BF16,
+ * 16-byte aligned, else ACS_EINVAL) into dev_p [rows] FP32. The kernel's
+ * only wait (for the tensor core's completion signal) is bounded; if it ever
+ * gives up, the rows that were not scored hold NaN. */
 acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, int64_t rows,
                            float* dev_p, void* stream);
 

@@ -2,7 +2,10 @@
 // tensor-core MLP (forward, fused forward+backward, Adam) and the pruning /
 // reweighting of the candidate rows. See include/acs_prior.h.
 //
-// Tensor-core layout. A warp handles 16 feature rows (edges) at a time with
+// Scoring (acs_mlp_forward) runs on tcgen05 with the accumulators in tensor
+// memory; its layout is described above mlp_forward_tc_kernel.
+//
+// Training layout. A warp handles 16 feature rows (edges) at a time with
 // mma.sync m16n8k16 (BF16 operands, FP32 accumulators):
 //   layer 1: [16 x 16] x [16 x 64]   (8 features zero-padded to K = 16)
 //   layer 2: [16 x 64] x [64 x 64]
@@ -17,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <new>
 
@@ -198,23 +202,273 @@ __device__ __forceinline__ float bce_term(float z, float y)
     return fmaxf(z, 0.0f) - z * y + log1pf(expf(-fabsf(z)));
 }
 
-__global__ void mlp_forward_kernel(const float* P, const uint16_t* feat, int64_t rows, float* pout)
+// ---------------------------------------------------------------------------
+// Scoring forward pass on the 5th-generation tensor cores (tcgen05).
+//
+// One CTA of four warps scores 128 feature rows per tile: row t of the tile
+// is thread t and TMEM lane t. The operands sit in shared memory in the
+// canonical K-major layout without swizzle: 8 x 8 BF16 core matrices of 128
+// contiguous bytes (8 rows of 16 B), K-adjacent core matrices 128 B apart
+// (leading byte offset) and 8-row groups (K/8) x 128 B apart (stride byte
+// offset). One thread issues
+//   layer 1: D1[128 x 64] = X[128 x 16] W1   (one MMA; K 8..15 zero)
+//   layer 2: D2[128 x 64] = H1[128 x 64] W2  (four MMAs of K = 16)
+// into FP32 accumulators in TMEM columns 0-63 (D1) and 64-127 (D2), and
+// commits each layer to an mbarrier. The epilogues read the accumulators back
+// with tcgen05.ld (each warp its 32 lanes): layer 1 adds b1, applies ReLU and
+// writes H1 in BF16 into shared memory as the A operand of layer 2; layer 2
+// adds b2, applies ReLU and takes the dot product with w3 in FP32 (N = 1
+// stays on the CUDA cores). Same rounding points as the training kernel.
+
+constexpr int kTcRows = 128;
+constexpr uint32_t kTmemCols = 128;
+constexpr size_t kTcSmem = 48 * 1024;   // also caps residency at 4 CTAs (512 TMEM columns) per SM
+constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bound of one MMA-completion wait
+// instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28
+constexpr uint32_t kIdescM128N64 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct TcSmem {
+    uint16_t x[kTcRows * 16];    // layer-1 A: 16 row groups x 2 K groups
+    uint16_t h1[kTcRows * 64];   // layer-2 A: 16 row groups x 8 K groups
+    uint16_t w1[64 * 16];        // layer-1 B = W1^T: 8 row groups (outputs) x 2 K groups
+    uint16_t w2[64 * 64];        // layer-2 B = W2^T: 8 x 8
+    float b1[64], b2[64], w3[64];
+    float b3;
+    uint32_t tmem;               // TMEM base address written by tcgen05.alloc
+    unsigned long long bar;      // MMA completion barrier
+};
+static_assert(sizeof(TcSmem) <= kTcSmem, "scoring tile does not fit");
+static_assert(offsetof(TcSmem, h1) % 128 == 0 && offsetof(TcSmem, w1) % 128 == 0 &&
+                  offsetof(TcSmem, w2) % 128 == 0,
+              "operand tiles must start on core-matrix boundaries");
+
+// element index of (row r, column k) in a K-major no-swizzle tile with kg K groups
+__device__ __forceinline__ int core_idx(int r, int k, int kg)
 {
-    __shared__ MlpSmem S;
-    load_weights(S, P, false);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t tiles = (rows + 15) / 16;
-    for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tile < tiles;
-         tile += warps) {
-        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-        Fwd F;
-        mlp_fwd_tile(S, feat, r0 < rows ? r0 : -1, r1 < rows ? r1 : -1, F);
-        if (t == 0) {
-            if (r0 < rows) pout[r0] = sigmoidf(F.z0);
-            if (r1 < rows) pout[r1] = sigmoidf(F.z1);
+    return (((r >> 3) * kg + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
+// byte offset >> 4 (bits 16-29) = 128 B, stride byte offset >> 4 (bits 32-45),
+// descriptor version 1 (bits 46-48), base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t sbo)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                 :
+                 : "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// generic-proxy writes to shared memory -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Waits for the completion of phase `parity` of the barrier; gives up after
+// kWaitNs of wall time (%globaltimer) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    unsigned long long t0 = 0ull;
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if (t0 == 0ull) t0 = now;
+        else if (now - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ uint4 load_feat(const uint16_t* feat, int64_t row, int64_t rows)
+{
+    return row < rows ? __ldg(reinterpret_cast<const uint4*>(feat) + row) : make_uint4(0u, 0u, 0u, 0u);
+}
+
+__global__ void __launch_bounds__(128)
+mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float* pout)
+{
+    extern __shared__ __align__(128) unsigned char tsm[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tsm);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    int64_t tile = blockIdx.x;
+    uint4 xv = load_feat(feat, tile * kTcRows + tid, rows);   // first tile's row, in flight during the set-up
+    {
+        // Weights: all loads issued before any is used (coalesced over the
+        // outputs); 8 consecutive K values of one output form one 16-byte
+        // row of a core matrix. Thread (out, c0) packs K groups c0, c0+2,
+        // c0+4, c0+6 of W2^T; threads 0-63 also W1^T, threads 64-127 the
+        // biases and w3.
+        const int out = tid & 63, c0 = tid >> 6;
+        float w[4][8], u[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[q][j] = __ldg(P + kW2 + ((c0 + 2 * q) * 8 + j) * 64 + out);
+        if (tid < 64) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) u[j] = __ldg(P + kW1 + j * 64 + out);
+        } else {
+            u[0] = __ldg(P + kB1 + out);
+            u[1] = __ldg(P + kB2 + out);
+            u[2] = __ldg(P + kW3 + out);
+            u[3] = out == 0 ? __ldg(P + kB3) : 0.0f;
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(&S.w2[core_idx(out, (c0 + 2 * q) * 8, 8)]) =
+                make_uint4(pack_bf16(w[q][0], w[q][1]), pack_bf16(w[q][2], w[q][3]),
+                           pack_bf16(w[q][4], w[q][5]), pack_bf16(w[q][6], w[q][7]));
+        if (tid < 64) {
+            *reinterpret_cast<uint4*>(&S.w1[core_idx(out, 0, 2)]) =
+                make_uint4(pack_bf16(u[0], u[1]), pack_bf16(u[2], u[3]), pack_bf16(u[4], u[5]),
+                           pack_bf16(u[6], u[7]));
+            *reinterpret_cast<uint4*>(&S.w1[core_idx(out, 8, 2)]) = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            S.b1[out] = u[0];
+            S.b2[out] = u[1];
+            S.w3[out] = u[2];
+            if (out == 0) S.b3 = u[3];
+        }
+    }
+    // K 8..15 of the layer-1 A tile stay zero
+    *reinterpret_cast<uint4*>(&S.x[core_idx(tid, 8, 2)]) = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&S.tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 TMEM lanes
+    const uint64_t da1 = smem_desc(S.x, 256), db1 = smem_desc(S.w1, 256);
+    const uint64_t da2 = smem_desc(S.h1, 1024), db2 = smem_desc(S.w2, 1024);
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+    const int64_t stride = (int64_t)gridDim.x * kTcRows;
+    uint32_t parity = 0;
+    bool ok = true;
+    for (; tile < tiles; tile += gridDim.x) {
+        const int64_t row = tile * kTcRows + tid;
+        *reinterpret_cast<uint4*>(&S.x[core_idx(tid, 0, 2)]) = xv;
+        xv = load_feat(feat, row + stride, rows);   // next tile's row, in flight during this one
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            tc_mma(tmem, da1, db1, kIdescM128N64, 0u);
+            tc_commit(bar);
+        }
+        ok = mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) break;
+        parity ^= 1u;
+        tc_fence_after();
+        float v[64];
+        tc_ld32(lanes, v);
+        tc_ld32(lanes + 32, v + 32);
+        tc_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint32_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = c * 8 + j * 2;
+                q[j] = pack_bf16(fmaxf(v[k] + S.b1[k], 0.0f), fmaxf(v[k + 1] + S.b1[k + 1], 0.0f));
+            }
+            *reinterpret_cast<uint4*>(&S.h1[core_idx(tid, c * 8, 8)]) = make_uint4(q[0], q[1], q[2], q[3]);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)   // K step of 16 = 256 B = 16 in the address field
+                tc_mma(tmem + 64, da2 + 16u * kk, db2 + 16u * kk, kIdescM128N64, kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+        }
+        ok = mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) break;
+        parity ^= 1u;
+        tc_fence_after();
+        tc_ld32(lanes + 64, v);
+        tc_ld32(lanes + 96, v + 32);
+        tc_wait_ld();
+        float z = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 64; ++c) z += fmaxf(v[c] + S.b2[c], 0.0f) * S.w3[c];
+        if (row < rows) pout[row] = sigmoidf(z + S.b3);
+        tc_fence_before();
+    }
+    if (!ok) {
+        // a wait gave up: allow the MMA in flight one more bounded wait, and
+        // leave NaN in every row of this CTA that was not scored
+        mbar_wait(bar, parity);
+        for (; tile < tiles; tile += gridDim.x) {
+            const int64_t row = tile * kTcRows + tid;
+            if (row < rows) pout[row] = __int_as_float(0x7fc00000);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
     }
 }
 
@@ -564,10 +818,17 @@ acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, in
                            void* stream)
 {
     if (rows == 0) return ACS_OK;
-    if (!dev_params || !dev_feat || !dev_p || rows < 0) return ACS_EINVAL;
-    const int64_t tiles = (rows + 15) / 16;
-    const int grid = (int)(tiles / 8 + 1 < 4096 ? tiles / 8 + 1 : 4096);
-    mlp_forward_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(dev_params, dev_feat, rows, dev_p);
+    if (!dev_params || !dev_feat || !dev_p || rows < 0 || ((uintptr_t)dev_feat & 15)) return ACS_EINVAL;
+    if (cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
+        cudaSuccess)
+        return ACS_ECUDA;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // persistent: at most 4 resident CTAs per SM (shared memory and TMEM)
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+    const int grid = (int)(tiles < 4 * (int64_t)sms ? tiles : 4 * (int64_t)sms);
+    mlp_forward_tc_kernel<<<grid, kTcRows, kTcSmem, (cudaStream_t)stream>>>(dev_params, dev_feat, rows, dev_p);
     return launched(cudaGetLastError());
 }
 

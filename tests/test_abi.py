@@ -123,6 +123,7 @@ def test_prior_calls_reject_bad_arguments_on_host(lib):
     assert lib.acs_mlp_forward(fake, fake, -1, fake, None) == E
     assert lib.acs_mlp_forward(None, fake, 5, fake, None) == E
     assert lib.acs_mlp_forward(None, None, 0, None, None) == acs.ACS_OK   # nothing to do
+    assert lib.acs_mlp_forward(fake, vp(0x1008), 5, fake, None) == E   # feature rows not 16-byte aligned
     assert lib.acs_mlp_train_batch(fake, fake, fake, 0, 0, 1, 1, 0, fake, fake, None) == E
     assert lib.acs_mlp_train_batch(fake, fake, fake, 10, 0, 0, 1, 0, fake, fake, None) == E
     assert lib.acs_mlp_train_batch(fake, fake, fake, 10, 0, 4, 0, 0, fake, fake, None) == E

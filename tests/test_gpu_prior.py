@@ -110,6 +110,40 @@ def test_forward_matches_fp64(oracle_mod, rows):
     assert np.all((p > 0) & (p < 1))
 
 
+def _forward_bf16_points(P, bits):
+    """The forward with the kernel's rounding points: W1, W2 and h1 rounded to
+    BF16 (nearest-even), everything else FP64. Differs from the kernel only by
+    FP32 accumulation order and, rarely, a BF16 rounding of h1 that an FP32
+    sum puts on the other side of a rounding boundary."""
+    def bf(a):
+        return _bits_to_f64(_bf16_bits(np.asarray(a, np.float32)))
+
+    x = _bits_to_f64(bits)
+    h1 = bf(np.maximum(x @ bf(P["W1"]) + P["b1"], 0.0))
+    h2 = np.maximum(h1 @ bf(P["W2"]) + P["b2"], 0.0)
+    z = h2 @ P["w3"].reshape(-1) + P["b3"][0]
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+@pytest.mark.parametrize("rows", [128, 129, 32064, 200000])
+def test_forward_matches_bf16_rounding_points(oracle_mod, rows):
+    """Tight check of the tensor-core layers: every tile row, every hidden
+    unit and both K halves of layer 2 must land in the right place, so a
+    transposed operand or a misplaced core matrix fails by far more than
+    the bound. Sizes span one full tile, a ragged second tile and more
+    tiles than the persistent grid has CTAs."""
+    prior = _prior()
+    base = _edge_rows(instances.clustered(1002, seed=3))
+    x = np.tile(base, (rows // base.shape[0] + 1, 1))[:rows]
+    x = x * np.random.default_rng(rows).uniform(0.5, 1.5, x.shape)
+    bits = _bf16_bits(x)
+    P = _params64(7)
+    p = prior.score(_dev(prior.pack(P)), _dev(bits.view(np.int16).reshape(rows, 8))).cpu().numpy()
+    err = np.abs(p.astype(np.float64) - _forward_bf16_points(P, bits))
+    assert np.quantile(err, 0.99) <= 1e-5, float(np.quantile(err, 0.99))
+    assert err.max() <= 5e-3, float(err.max())
+
+
 def test_forward_zero_weights_is_sigmoid_of_bias():
     prior = _prior()
     v = np.zeros(acs.ACS_MLP_PARAMS, np.float32)
