@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 CL = 32
 MEM_NAMES = {0: "matrix", 1: "spm"}
 HBM_PEAK_FALLBACK = 6800.0
+BF16_PEAK_FALLBACK = 1900.0   # TFLOP/s, dense bf16 burst of an earlier GB300 measurement
 
 # Workloads (synthetic stand-ins for the paper's TSPLIB instances). The default
 # is the paper-scale configuration; the others are the single-instance, batched
@@ -123,7 +124,7 @@ def measured_peaks():
         with open(path) as f:
             return json.load(f), "measured"
     except Exception:
-        return {"hbm_gbs": HBM_PEAK_FALLBACK}, "fallback"
+        return {"hbm_gbs": HBM_PEAK_FALLBACK, "bf16_tflops": BF16_PEAK_FALLBACK}, "fallback"
 
 
 class ClockSampler:
@@ -415,6 +416,48 @@ def gap_leg(iters, log=None):
     }
 
 
+SCORING_ROWS = 1 << 24   # 16.8 M candidate edges (n = 524,288 nodes x 32): 335 MB in and out, > L2
+SCORING_FLOPS_USEFUL = 2 * (8 * 64 + 64 * 64 + 64)      # per edge: the three layers
+SCORING_FLOPS_ISSUED = 2 * 64 * (16 + 80)                # per edge on the tensor core (K padded, bias columns)
+
+
+def prior_scoring_leg(steps, warmup):
+    """The learned prior's scoring kernel (tcgen05, acs_mlp_forward) on
+    SCORING_ROWS seeded synthetic BF16 feature rows, timed alone with CUDA
+    events on its stream. Inputs are larger than L2."""
+    import torch
+
+    from paper_1605_02669_gb300 import acs
+
+    st = torch.cuda.Stream()
+    g = torch.Generator(device="cuda").manual_seed(11)
+    with torch.cuda.stream(st):
+        params = (torch.randn(acs.ACS_MLP_PARAMS, device="cuda", generator=g) * 0.2).float()
+        feat = torch.randn(SCORING_ROWS, 8, device="cuda", generator=g).to(torch.bfloat16).view(torch.int16)
+        p = torch.empty(SCORING_ROWS, device="cuda")
+    for _ in range(warmup):
+        acs.acs_mlp_forward(params, feat, SCORING_ROWS, p, st.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        acs.acs_mlp_forward(params, feat, SCORING_ROWS, p, st.cuda_stream)
+    e1.record(st)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1000.0 / steps
+    peaks, kind = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", BF16_PEAK_FALLBACK))
+    tflops = SCORING_ROWS * SCORING_FLOPS_USEFUL / sec * 1e-12
+    return {"kernel": "mlp_forward_tc_kernel (tcgen05, TMEM accumulators)", "rows": SCORING_ROWS,
+            "us_per_launch": sec * 1e6, "edges_per_s": SCORING_ROWS / sec,
+            "issued_tflops": SCORING_ROWS * SCORING_FLOPS_ISSUED / sec * 1e-12,
+            "hbm_gbs": SCORING_ROWS * 20 / sec * 1e-9,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "peak_kind": kind + " bf16 burst",
+                         "flops_per_edge": SCORING_FLOPS_USEFUL},
+            "data": "synthetic N(0,1) features rounded to BF16, random N(0,0.2) weights"}
+
+
 def relaxed_leg(xy, off, steps, warmup):
     """The relaxed construction (ACS-GPU-Alt, Sec. 3.1.2) on the same instances,
     pheromone matrix: no step barrier, racy local updates (not bit-exact),
@@ -599,6 +642,7 @@ def run_ours(args, rank, world, local):
         return None
     gap = None if (args.no_gap or WORKLOAD != "paper") else gap_leg(args.gap_iters)
     relaxed = None if args.no_relaxed else relaxed_leg(xy, off, args.steps, args.warmup)
+    scoring = None if args.no_prior_scoring else prior_scoring_leg(args.steps, args.warmup)
     cpu = None if args.no_cpu_baseline else cpu_baseline_leg()
     return {
         "metric": "ant-steps/s in tour construction",
@@ -624,6 +668,7 @@ def run_ours(args, rank, world, local):
         "tuning": tuning,
         "gap_at_equal_time": gap,
         "relaxed": relaxed,
+        "prior_scoring": scoring,
     }
 
 
@@ -645,12 +690,24 @@ def main():
                     help="skip the relaxed-construction leg")
     ap.add_argument("--gap-iters", type=int, default=1000,
                     help="iterations of the plain colony in the gap leg")
+    ap.add_argument("--no-prior-scoring", action="store_true",
+                    help="skip the learned prior's scoring leg")
+    ap.add_argument("--prior-scoring-only", action="store_true",
+                    help="run only the learned prior's scoring leg (profiling)")
     ap.add_argument("--tpa", type=int, default=0, help="pin lanes per ant instead of autotuning")
     ap.add_argument("--cluster", type=int, default=0, help="pin the cluster size instead of autotuning")
     args = ap.parse_args()
     select_workload(args.workload)
     rank, world, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.prior_scoring_only:
+        import torch
+
+        torch.cuda.set_device(local)
+        import __graft_entry__
+
+        __graft_entry__.build()
+        out = prior_scoring_leg(args.steps, args.warmup) if rank == 0 else None
+    elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         out = run_ours(args, rank, world, local)

@@ -205,24 +205,29 @@ __device__ __forceinline__ float bce_term(float z, float y)
 // ---------------------------------------------------------------------------
 // Scoring forward pass on the 5th-generation tensor cores (tcgen05).
 //
-// One CTA of four warps scores 128 feature rows per tile: row t of the tile
-// is thread t and TMEM lane t. The operands sit in shared memory in the
-// canonical K-major layout without swizzle: 8 x 8 BF16 core matrices of 128
-// contiguous bytes (8 rows of 16 B), K-adjacent core matrices 128 B apart
-// (leading byte offset) and 8-row groups (K/8) x 128 B apart (stride byte
-// offset). One thread issues
-//   layer 1: D1[128 x 64] = X[128 x 16] W1   (one MMA; K 8..15 zero)
-//   layer 2: D2[128 x 64] = H1[128 x 64] W2  (four MMAs of K = 16)
-// into FP32 accumulators in TMEM columns 0-63 (D1) and 64-127 (D2), and
-// commits each layer to an mbarrier. The epilogues read the accumulators back
-// with tcgen05.ld (each warp its 32 lanes): layer 1 adds b1, applies ReLU and
-// writes H1 in BF16 into shared memory as the A operand of layer 2; layer 2
-// adds b2, applies ReLU and takes the dot product with w3 in FP32 (N = 1
-// stays on the CUDA cores). Same rounding points as the training kernel.
+// A CTA holds G groups of four warps (G <= 8) that share the weights in
+// shared memory; each group scores 128 feature rows per tile (row t of the
+// tile is the group's thread t and TMEM lane t) and walks its own sequence
+// of tiles, so G tile chains are in flight per CTA. The operands sit in
+// shared memory in the canonical K-major layout without swizzle: 8 x 8 BF16
+// core matrices of 128 contiguous bytes (8 rows of 16 B), K-adjacent core
+// matrices 128 B apart (leading byte offset) and 8-row groups (K/8) x 128 B
+// apart (stride byte offset). One thread of the group issues
+//   layer 1: D[128 x 64] = [X | 1 1 1 0..][128 x 16] [W1 ; b1 split][16 x 64]
+//   layer 2: D[128 x 64] = [H1 | 1 1 1 0..][128 x 80] [W2 ; b2 split][80 x 64]
+// (one MMA, then five of K = 16) into the group's 64 FP32 TMEM columns, and
+// commits each layer to the group's mbarrier. The biases ride in the K
+// padding: each FP32 bias is split exactly into three BF16 parts that meet
+// three constant-one columns, so the accumulator adds the bias in FP32. The
+// epilogues read the accumulator back with tcgen05.ld (each warp its 32
+// lanes): layer 1 rounds to BF16, applies ReLU and writes H1 into shared
+// memory as the A operand of layer 2; layer 2 applies ReLU and takes the dot
+// product with w3 in FP32 (N = 1 stays on the CUDA cores). Rounding points
+// as in the training kernel: BF16 operands, FP32 accumulation, h2 in FP32.
 
 constexpr int kTcRows = 128;
-constexpr uint32_t kTmemCols = 128;
-constexpr size_t kTcSmem = 48 * 1024;   // also caps residency at 4 CTAs (512 TMEM columns) per SM
+constexpr int kTcMaxGroups = 8;
+constexpr int kK1 = 16, kK2 = 80;   // K of layer 1 (8 features, 3 bias columns) and layer 2 (64 + 3)
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bound of one MMA-completion wait
 // instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
@@ -230,20 +235,32 @@ constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bound of one M
 constexpr uint32_t kIdescM128N64 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-struct TcSmem {
-    uint16_t x[kTcRows * 16];    // layer-1 A: 16 row groups x 2 K groups
-    uint16_t h1[kTcRows * 64];   // layer-2 A: 16 row groups x 8 K groups
-    uint16_t w1[64 * 16];        // layer-1 B = W1^T: 8 row groups (outputs) x 2 K groups
-    uint16_t w2[64 * 64];        // layer-2 B = W2^T: 8 x 8
-    float b1[64], b2[64], w3[64];
+struct TcWeights {
+    uint16_t w1[64 * kK1];   // layer-1 B = [W1 ; b1]^T: 8 row groups (outputs) x 2 K groups
+    uint16_t w2[64 * kK2];   // layer-2 B = [W2 ; b2]^T: 8 x 10
+    float w3[64];
     float b3;
-    uint32_t tmem;               // TMEM base address written by tcgen05.alloc
-    unsigned long long bar;      // MMA completion barrier
+    uint32_t tmem;           // TMEM base address written by tcgen05.alloc
 };
-static_assert(sizeof(TcSmem) <= kTcSmem, "scoring tile does not fit");
-static_assert(offsetof(TcSmem, h1) % 128 == 0 && offsetof(TcSmem, w1) % 128 == 0 &&
-                  offsetof(TcSmem, w2) % 128 == 0,
+struct TcGroup {
+    uint16_t x[kTcRows * kK1];    // layer-1 A: 16 row groups x 2 K groups
+    uint16_t h1[kTcRows * kK2];   // layer-2 A: 16 row groups x 10 K groups
+    unsigned long long bar;       // MMA completion barrier
+};
+constexpr size_t kTcWeightBytes = (sizeof(TcWeights) + 127) & ~size_t(127);
+constexpr size_t kTcGroupBytes = (sizeof(TcGroup) + 127) & ~size_t(127);
+constexpr size_t tc_smem(int groups) { return kTcWeightBytes + groups * kTcGroupBytes; }
+static_assert(tc_smem(kTcMaxGroups) <= 227 * 1024, "scoring CTA does not fit");
+static_assert(offsetof(TcWeights, w2) % 128 == 0 && offsetof(TcGroup, h1) % 128 == 0,
               "operand tiles must start on core-matrix boundaries");
+
+// TMEM columns of a CTA of G groups (64 each, a power of two >= 32). With
+// the shared memory of tc_smem(G) at most 512 columns are held per SM:
+// G = 1: 6 CTAs x 64; G = 2: 3 x 128; G = 3, 4: 2 x 256; G >= 5: 1 x 512.
+constexpr uint32_t tc_tmem_cols(int groups)
+{
+    return groups <= 1 ? 64u : groups <= 2 ? 128u : groups <= 4 ? 256u : 512u;
+}
 
 // element index of (row r, column k) in a K-major no-swizzle tile with kg K groups
 __device__ __forceinline__ int core_idx(int r, int k, int kg)
@@ -283,6 +300,23 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 // generic-proxy writes to shared memory -> visible to the tensor core (async proxy)
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// the 128 threads of one group meet at named barrier `id` (1..8)
+__device__ __forceinline__ void group_sync(int id)
+{
+    asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ bool group_sync_or(int id, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id)
+        : "memory");
+    return r != 0u;
+}
 
 // 32 consecutive FP32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32])
@@ -329,63 +363,79 @@ __device__ __forceinline__ uint4 load_feat(const uint16_t* feat, int64_t row, in
     return row < rows ? __ldg(reinterpret_cast<const uint4*>(feat) + row) : make_uint4(0u, 0u, 0u, 0u);
 }
 
-__global__ void __launch_bounds__(128)
-mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float* pout)
+__device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float bf16_value(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// One 16-byte core-matrix row holding the three BF16 parts of an FP32 bias
+// (hi + mid + lo == b exactly: each part takes the next 8 significant bits)
+// followed by zeros; with `ones` the row of constant-one columns instead.
+__device__ __forceinline__ uint4 bias_row(float b, bool ones)
+{
+    if (ones) return make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);
+    const uint16_t hi = bf16_bits(b);
+    const float r1 = b - bf16_value(hi);
+    const uint16_t mid = bf16_bits(r1);
+    const uint16_t lo = bf16_bits(r1 - bf16_value(mid));
+    return make_uint4((uint32_t)hi | ((uint32_t)mid << 16), (uint32_t)lo, 0u, 0u);
+}
+
+__global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
+mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float* pout, uint32_t tmem_cols)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
-    TcSmem& S = *reinterpret_cast<TcSmem*>(tsm);
+    TcWeights& W = *reinterpret_cast<TcWeights*>(tsm);
     const int tid = threadIdx.x, warp = tid >> 5;
-    int64_t tile = blockIdx.x;
-    uint4 xv = load_feat(feat, tile * kTcRows + tid, rows);   // first tile's row, in flight during the set-up
-    {
-        // Weights: all loads issued before any is used (coalesced over the
-        // outputs); 8 consecutive K values of one output form one 16-byte
-        // row of a core matrix. Thread (out, c0) packs K groups c0, c0+2,
-        // c0+4, c0+6 of W2^T; threads 0-63 also W1^T, threads 64-127 the
-        // biases and w3.
-        const int out = tid & 63, c0 = tid >> 6;
-        float w[4][8], u[8];
+    const int g = tid >> 7, t = tid & (kTcRows - 1);   // group, row of the group's tile
+    const int groups = blockDim.x >> 7;
+    TcGroup& G = *reinterpret_cast<TcGroup*>(tsm + kTcWeightBytes + g * kTcGroupBytes);
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+    const int64_t gstride = (int64_t)gridDim.x * groups;
+    int64_t tile = (int64_t)blockIdx.x * groups + g;
+    uint4 xv = load_feat(feat, tile * kTcRows + t, rows);   // first tile's row, in flight during the set-up
+    // Weights, all loads issued before any is used (coalesced over the
+    // outputs); 8 consecutive K values of one output form one 16-byte row of
+    // a core matrix. Item i < 512: K group i / 64 of output i % 64 of W2;
+    // 512-575: W1 and b1 of output i - 512; 576-639: b2; 640-703: w3, b3.
+    for (int i = tid; i < 704; i += blockDim.x) {
+        const int out = i & 63;
+        if (i < 512) {
+            const int c = i >> 6;
+            float w[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+            for (int j = 0; j < 8; ++j) w[j] = __ldg(P + kW2 + (c * 8 + j) * 64 + out);
+            *reinterpret_cast<uint4*>(&W.w2[core_idx(out, c * 8, kK2 / 8)]) =
+                make_uint4(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]), pack_bf16(w[4], w[5]),
+                           pack_bf16(w[6], w[7]));
+        } else if (i < 576) {
+            float w[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) w[q][j] = __ldg(P + kW2 + ((c0 + 2 * q) * 8 + j) * 64 + out);
-        if (tid < 64) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) u[j] = __ldg(P + kW1 + j * 64 + out);
+            for (int j = 0; j < 8; ++j) w[j] = __ldg(P + kW1 + j * 64 + out);
+            const float b = __ldg(P + kB1 + out);
+            *reinterpret_cast<uint4*>(&W.w1[core_idx(out, 0, kK1 / 8)]) =
+                make_uint4(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]), pack_bf16(w[4], w[5]),
+                           pack_bf16(w[6], w[7]));
+            *reinterpret_cast<uint4*>(&W.w1[core_idx(out, 8, kK1 / 8)]) = bias_row(b, false);
+        } else if (i < 640) {
+            *reinterpret_cast<uint4*>(&W.w2[core_idx(out, 64, kK2 / 8)]) = bias_row(__ldg(P + kB2 + out), false);
+            *reinterpret_cast<uint4*>(&W.w2[core_idx(out, 72, kK2 / 8)]) = make_uint4(0u, 0u, 0u, 0u);
         } else {
-            u[0] = __ldg(P + kB1 + out);
-            u[1] = __ldg(P + kB2 + out);
-            u[2] = __ldg(P + kW3 + out);
-            u[3] = out == 0 ? __ldg(P + kB3) : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(&S.w2[core_idx(out, (c0 + 2 * q) * 8, 8)]) =
-                make_uint4(pack_bf16(w[q][0], w[q][1]), pack_bf16(w[q][2], w[q][3]),
-                           pack_bf16(w[q][4], w[q][5]), pack_bf16(w[q][6], w[q][7]));
-        if (tid < 64) {
-            *reinterpret_cast<uint4*>(&S.w1[core_idx(out, 0, 2)]) =
-                make_uint4(pack_bf16(u[0], u[1]), pack_bf16(u[2], u[3]), pack_bf16(u[4], u[5]),
-                           pack_bf16(u[6], u[7]));
-            *reinterpret_cast<uint4*>(&S.w1[core_idx(out, 8, 2)]) = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-            S.b1[out] = u[0];
-            S.b2[out] = u[1];
-            S.w3[out] = u[2];
-            if (out == 0) S.b3 = u[3];
+            W.w3[out] = __ldg(P + kW3 + out);
+            if (out == 0) W.b3 = __ldg(P + kB3);
         }
     }
-    // K 8..15 of the layer-1 A tile stay zero
-    *reinterpret_cast<uint4*>(&S.x[core_idx(tid, 8, 2)]) = make_uint4(0u, 0u, 0u, 0u);
-    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
-    if (tid == 0) {
+    // constant-one columns of the group's A tiles (never overwritten)
+    *reinterpret_cast<uint4*>(&G.x[core_idx(t, 8, kK1 / 8)]) = bias_row(0.0f, true);
+    *reinterpret_cast<uint4*>(&G.h1[core_idx(t, 64, kK2 / 8)]) = bias_row(0.0f, true);
+    *reinterpret_cast<uint4*>(&G.h1[core_idx(t, 72, kK2 / 8)]) = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&G.bar);
+    if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
-        const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&S.tmem);
+        const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&W.tmem);
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot),
-                     "r"(kTmemCols)
+                     "r"(tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -393,73 +443,80 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = S.tmem;
-    const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 TMEM lanes
-    const uint64_t da1 = smem_desc(S.x, 256), db1 = smem_desc(S.w1, 256);
-    const uint64_t da2 = smem_desc(S.h1, 1024), db2 = smem_desc(S.w2, 1024);
-    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
-    const int64_t stride = (int64_t)gridDim.x * kTcRows;
+    const uint32_t tmem = W.tmem;
+    const uint32_t dcol = tmem + 64u * g;                                  // the group's accumulator
+    const uint32_t lanes = dcol + ((uint32_t)((warp & 3) * 32) << 16);     // this warp's 32 lanes of it
+    const uint64_t da1 = smem_desc(G.x, (kK1 / 8) * 128), db1 = smem_desc(W.w1, (kK1 / 8) * 128);
+    const uint64_t da2 = smem_desc(G.h1, (kK2 / 8) * 128), db2 = smem_desc(W.w2, (kK2 / 8) * 128);
+    const int bid = 1 + g;   // the group's named barrier
     uint32_t parity = 0;
     bool ok = true;
-    for (; tile < tiles; tile += gridDim.x) {
-        const int64_t row = tile * kTcRows + tid;
-        *reinterpret_cast<uint4*>(&S.x[core_idx(tid, 0, 2)]) = xv;
-        xv = load_feat(feat, row + stride, rows);   // next tile's row, in flight during this one
+    for (; tile < tiles; tile += gstride) {
+        const int64_t row = tile * kTcRows + t;
+        *reinterpret_cast<uint4*>(&G.x[core_idx(t, 0, kK1 / 8)]) = xv;
+        xv = load_feat(feat, row + gstride * kTcRows, rows);   // next tile's row, in flight during this one
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        group_sync(bid);
+        if (t == 0) {
             tc_fence_after();
-            tc_mma(tmem, da1, db1, kIdescM128N64, 0u);
+            tc_mma(dcol, da1, db1, kIdescM128N64, 0u);
             tc_commit(bar);
         }
         ok = mbar_wait(bar, parity);
-        if (__syncthreads_or(!ok)) break;
+        if (group_sync_or(bid, !ok)) break;
         parity ^= 1u;
         tc_fence_after();
-        float v[64];
-        tc_ld32(lanes, v);
-        tc_ld32(lanes + 32, v + 32);
-        tc_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            uint32_t q[4];
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tc_ld32(lanes + 32 * half, v);
+            tc_wait_ld();
+            const __nv_bfloat162 zero2 = __float2bfloat162_rn(0.0f);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int k = c * 8 + j * 2;
-                q[j] = pack_bf16(fmaxf(v[k] + S.b1[k], 0.0f), fmaxf(v[k + 1] + S.b1[k + 1], 0.0f));
+            for (int c = 0; c < 4; ++c) {
+                uint32_t q[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(v[c * 8 + 2 * j], v[c * 8 + 2 * j + 1]), zero2);
+                    q[j] = *reinterpret_cast<const uint32_t*>(&h);
+                }
+                *reinterpret_cast<uint4*>(&G.h1[core_idx(t, (half * 4 + c) * 8, kK2 / 8)]) =
+                    make_uint4(q[0], q[1], q[2], q[3]);
             }
-            *reinterpret_cast<uint4*>(&S.h1[core_idx(tid, c * 8, 8)]) = make_uint4(q[0], q[1], q[2], q[3]);
         }
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        group_sync(bid);
+        if (t == 0) {
             tc_fence_after();
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)   // K step of 16 = 256 B = 16 in the address field
-                tc_mma(tmem + 64, da2 + 16u * kk, db2 + 16u * kk, kIdescM128N64, kk > 0 ? 1u : 0u);
+            for (int kk = 0; kk < kK2 / 16; ++kk)   // K step of 16 = 256 B = 16 in the address field
+                tc_mma(dcol, da2 + 16u * kk, db2 + 16u * kk, kIdescM128N64, kk > 0 ? 1u : 0u);
             tc_commit(bar);
         }
         ok = mbar_wait(bar, parity);
-        if (__syncthreads_or(!ok)) break;
+        if (group_sync_or(bid, !ok)) break;
         parity ^= 1u;
         tc_fence_after();
-        tc_ld32(lanes + 64, v);
-        tc_ld32(lanes + 96, v + 32);
-        tc_wait_ld();
-        float z = 0.0f;
+        float z = W.b3;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) z += fmaxf(v[c] + S.b2[c], 0.0f) * S.w3[c];
-        if (row < rows) pout[row] = sigmoidf(z + S.b3);
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tc_ld32(lanes + 32 * half, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 32; ++c) z = __fmaf_rn(fmaxf(v[c], 0.0f), W.w3[half * 32 + c], z);
+        }
+        if (row < rows) pout[row] = sigmoidf(z);
         tc_fence_before();
     }
     if (!ok) {
         // a wait gave up: allow the MMA in flight one more bounded wait, and
-        // leave NaN in every row of this CTA that was not scored
+        // leave NaN in every row of this group that was not scored
         mbar_wait(bar, parity);
-        for (; tile < tiles; tile += gridDim.x) {
-            const int64_t row = tile * kTcRows + tid;
+        for (; tile < tiles; tile += gstride) {
+            const int64_t row = tile * kTcRows + t;
             if (row < rows) pout[row] = __int_as_float(0x7fc00000);
         }
     }
@@ -467,7 +524,7 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols)
                      : "memory");
     }
 }
@@ -819,16 +876,22 @@ acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, in
 {
     if (rows == 0) return ACS_OK;
     if (!dev_params || !dev_feat || !dev_p || rows < 0 || ((uintptr_t)dev_feat & 15)) return ACS_EINVAL;
-    if (cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_smem(kTcMaxGroups)) != cudaSuccess)
         return ACS_ECUDA;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // persistent: at most 4 resident CTAs per SM (shared memory and TMEM)
+    if (sms < 1) return ACS_ECUDA;
+    // groups per CTA: enough to give every SM its share of the tiles, at most
+    // 8; persistent with one CTA per SM beyond 8 tiles per SM
     const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
-    const int grid = (int)(tiles < 4 * (int64_t)sms ? tiles : 4 * (int64_t)sms);
-    mlp_forward_tc_kernel<<<grid, kTcRows, kTcSmem, (cudaStream_t)stream>>>(dev_params, dev_feat, rows, dev_p);
+    const int64_t per_sm = (tiles + sms - 1) / sms;
+    const int groups = (int)(per_sm < kTcMaxGroups ? per_sm : kTcMaxGroups);
+    const int64_t ctas = (tiles + groups - 1) / groups;
+    const int grid = (int)(ctas < sms ? ctas : sms);
+    mlp_forward_tc_kernel<<<grid, kTcRows * groups, tc_smem(groups), (cudaStream_t)stream>>>(
+        dev_params, dev_feat, rows, dev_p, tc_tmem_cols(groups));
     return launched(cudaGetLastError());
 }
 

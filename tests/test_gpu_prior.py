@@ -125,13 +125,14 @@ def _forward_bf16_points(P, bits):
     return 1.0 / (1.0 + np.exp(-z))
 
 
-@pytest.mark.parametrize("rows", [128, 129, 32064, 200000])
+@pytest.mark.parametrize("rows", [128, 129, 32064, 50000, 76544, 120000, 200000])
 def test_forward_matches_bf16_rounding_points(oracle_mod, rows):
     """Tight check of the tensor-core layers: every tile row, every hidden
     unit and both K halves of layer 2 must land in the right place, so a
     transposed operand or a misplaced core matrix fails by far more than
-    the bound. Sizes span one full tile, a ragged second tile and more
-    tiles than the persistent grid has CTAs."""
+    the bound. Sizes span one full tile, a ragged second tile, CTAs of
+    2, 3, 4 and 7 tile groups, and more tiles than the persistent grid
+    has groups."""
     prior = _prior()
     base = _edge_rows(instances.clustered(1002, seed=3))
     x = np.tile(base, (rows // base.shape[0] + 1, 1))[:rows]
