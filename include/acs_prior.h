@@ -13,9 +13,10 @@
  *          -> z = h2 w3 + b3 -> p = sigmoid(z).
  * The two hidden layers run on the tensor cores with BF16 operands
  * (features, W1, h1, W2) and FP32 accumulation; biases, h2, w3 and the last
- * layer stay FP32. Scoring (acs_mlp_forward) issues tcgen05.mma with the
- * accumulators in tensor memory; training (acs_mlp_train_batch) uses
- * mma.sync m16n8k16 fragments in registers.
+ * layer stay FP32. Scoring (acs_mlp_forward) and training
+ * (acs_mlp_train_batch) issue tcgen05.mma with the accumulators in tensor
+ * memory; training rounds dh2 and dh1 to BF16 as the operands of the
+ * backward GEMMs and sums the bias and w3 gradients in FP32.
  *
  * Parameters are one FP32 device vector of ACS_MLP_PARAMS floats:
  *   W1 [8][64] at 0, b1 [64] at 512, W2 [64][64] at 576 (W2[in][out]),
@@ -70,7 +71,9 @@ acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, in
 /* One training pass over a mini-batch: rows b = 0..batch-1 read feature row
  * and label perm(first + b) with perm(i) = (perm_a * i + perm_c) mod total
  * (perm_a coprime with total). Writes the mean BCE loss to dev_loss[0] and
- * the gradient of that mean to dev_grad [ACS_MLP_PARAMS] (both overwritten). */
+ * the gradient of that mean to dev_grad [ACS_MLP_PARAMS] (both overwritten).
+ * dev_feat 16-byte aligned. If a bounded wait for the tensor core gives up,
+ * the loss is NaN and the gradient incomplete. */
 acs_status acs_mlp_train_batch(const float* dev_params, const uint16_t* dev_feat,
                                const float* dev_label, int64_t total, int64_t first,
                                int64_t batch, int64_t perm_a, int64_t perm_c, float* dev_grad,

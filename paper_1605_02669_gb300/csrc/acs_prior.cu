@@ -2,20 +2,11 @@
 // tensor-core MLP (forward, fused forward+backward, Adam) and the pruning /
 // reweighting of the candidate rows. See include/acs_prior.h.
 //
-// Scoring (acs_mlp_forward) runs on tcgen05 with the accumulators in tensor
-// memory; its layout is described above mlp_forward_tc_kernel.
-//
-// Training layout. A warp handles 16 feature rows (edges) at a time with
-// mma.sync m16n8k16 (BF16 operands, FP32 accumulators):
-//   layer 1: [16 x 16] x [16 x 64]   (8 features zero-padded to K = 16)
-//   layer 2: [16 x 64] x [64 x 64]
-//   layer 3: a dot product with w3 in FP32 on the CUDA cores (N = 1).
-// The FP32 accumulator fragment of one layer is, element for element, the
-// BF16 A fragment of the next layer, so activations never leave registers.
-// The backward pass recomputes the forward, forms dh2 and dh1 the same way,
-// and accumulates the weight gradients dW2 = h1^T dh2 and dW1 = x^T dh1 as
-// GEMMs over the 128 edges of a CTA block, reading the transposed operands
-// from shared memory with ldmatrix.trans.
+// Both the scoring forward pass (acs_mlp_forward) and the fused forward +
+// backward of training (acs_mlp_train_batch) run on the 5th-generation tensor
+// cores (tcgen05): BF16 operands in shared memory, FP32 accumulators in
+// tensor memory; their layouts are described above mlp_forward_tc_kernel and
+// mlp_train_kernel.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,158 +31,11 @@ using namespace acs;
 namespace {
 
 constexpr int kW1 = 0, kB1 = 512, kW2 = 576, kB2 = 4672, kW3 = 4736, kB3 = 4800;
-constexpr int kPadK1 = 24;   // smem row of W1^T: 16 K values + 8 pad (bank spread)
-constexpr int kPad64 = 72;   // smem row of a 64-wide BF16 tile: 64 + 8 pad
-constexpr int kBlockRows = 128;  // rows of a training block (8 warps x 16)
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const void* p)
-{
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
-
-// Weights as BF16 in shared memory, biases in FP32.
-struct MlpSmem {
-    uint16_t w1t[64][kPadK1];   // w1t[h][f] = W1[f][h], f >= 8 zero
-    uint16_t w2t[64][kPad64];   // w2t[out][in] = W2[in][out]  (forward B operand)
-    uint16_t w2[64][kPad64];    // w2[in][out]                  (backward B operand)
-    float w3[64];
-    float b1[64], b2[64], b3;
-};
-
-constexpr size_t round16(size_t x) { return (x + 15) & ~size_t(15); }
-// dynamic shared memory of the training kernel: weights, then the block's
-// x, h1, dh2 and dh1 tiles (16-byte aligned rows for ldmatrix), then the
-// bias / w3 gradient partials
-constexpr size_t kOffX = round16(sizeof(MlpSmem));
-constexpr size_t kOffH1 = kOffX + sizeof(uint16_t) * kBlockRows * kPadK1;
-constexpr size_t kOffRed = kOffH1 + 3 * sizeof(uint16_t) * kBlockRows * kPad64;
-constexpr size_t kTrainSmem = kOffRed + sizeof(float) * (3 * 64 + 1);
-static_assert(kOffH1 % 16 == 0 && kOffRed % 16 == 0, "ldmatrix rows need 16-byte alignment");
-
-__device__ void load_weights(MlpSmem& S, const float* P, bool need_w2)
-{
-    for (int i = threadIdx.x; i < 64 * kPadK1; i += blockDim.x) {
-        const int h = i / kPadK1, f = i - h * kPadK1;
-        const float v = f < 8 ? P[kW1 + f * 64 + h] : 0.0f;
-        S.w1t[h][f] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-    }
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-        const int in = i >> 6, out = i & 63;
-        const uint16_t v = __bfloat16_as_ushort(__float2bfloat16_rn(P[kW2 + i]));
-        S.w2t[out][in] = v;
-        if (need_w2) S.w2[in][out] = v;
-    }
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-        S.w3[i] = P[kW3 + i];
-        S.b1[i] = P[kB1 + i];
-        S.b2[i] = P[kB2 + i];
-    }
-    if (threadIdx.x == 0) S.b3 = P[kB3];
-}
-
-// Per-warp forward of 16 rows: lane (g, t) = (lane / 4, lane % 4) holds rows
-// g and g+8 of the tile (feature rows row0 and row1; absent when < 0). Leaves
-// in registers the relu masks, the h1 A fragments (BF16), h2 (FP32) and the
-// logits. Layer 3 (N = 1) runs in FP32 on the CUDA cores.
-struct Fwd {
-    uint32_t h1a[4][4];   // layer-2 A fragments (BF16 pairs), k-tile major
-    float h2[8][4];       // relu(h1 W2 + b2), C-fragment layout
-    uint32_t m1, m2;      // relu masks: bit nt*4+i of the C fragments
-    float z0, z1;         // logits of rows g and g+8
-};
-
-__device__ __forceinline__ void mlp_fwd_tile(const MlpSmem& S, const uint16_t* feat, int64_t row0,
-                                             int64_t row1, Fwd& F)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    // layer-1 A fragment: rows g and g+8, features t*2, t*2+1 (K 8..15 are zero)
-    uint32_t a[4];
-    a[0] = row0 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row0 * 8 + t * 2) : 0u;
-    a[1] = row1 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row1 * 8 + t * 2) : 0u;
-    a[2] = 0u;
-    a[3] = 0u;
-    float c1[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        c1[nt][0] = c1[nt][1] = c1[nt][2] = c1[nt][3] = 0.0f;
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w1t[nt * 8 + g][t * 2]);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w1t[nt * 8 + g][t * 2 + 8]);
-        mma16816(c1[nt], a, b0, b1);
-    }
-    F.m1 = 0u;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int col = nt * 8 + t * 2;
-        float v[4];
-        v[0] = c1[nt][0] + S.b1[col];
-        v[1] = c1[nt][1] + S.b1[col + 1];
-        v[2] = c1[nt][2] + S.b1[col];
-        v[3] = c1[nt][3] + S.b1[col + 1];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (v[i] > 0.0f) F.m1 |= 1u << (nt * 4 + i);
-            else v[i] = 0.0f;
-        }
-        // C fragment (rows g/g+8, cols col/col+1) -> A fragment of k-tile nt/2
-        const int kt = nt >> 1, hi = nt & 1;
-        F.h1a[kt][0 + 2 * hi] = pack_bf16(v[0], v[1]);
-        F.h1a[kt][1 + 2 * hi] = pack_bf16(v[2], v[3]);
-    }
-    float c2[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        c2[nt][0] = c2[nt][1] = c2[nt][2] = c2[nt][3] = 0.0f;
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&S.w2t[nt * 8 + g][kt * 16 + t * 2]);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&S.w2t[nt * 8 + g][kt * 16 + 8 + t * 2]);
-            mma16816(c2[nt], F.h1a[kt], b0, b1);
-        }
-    }
-    F.m2 = 0u;
-    float z0 = 0.0f, z1 = 0.0f;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int col = nt * 8 + t * 2;
-        float v[4];
-        v[0] = c2[nt][0] + S.b2[col];
-        v[1] = c2[nt][1] + S.b2[col + 1];
-        v[2] = c2[nt][2] + S.b2[col];
-        v[3] = c2[nt][3] + S.b2[col + 1];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (v[i] > 0.0f) F.m2 |= 1u << (nt * 4 + i);
-            F.h2[nt][i] = v[i] > 0.0f ? v[i] : 0.0f;
-        }
-        const float wa = S.w3[col], wb = S.w3[col + 1];
-        z0 += F.h2[nt][0] * wa + F.h2[nt][1] * wb;
-        z1 += F.h2[nt][2] * wa + F.h2[nt][3] * wb;
-    }
-    // the four lanes of a quad hold the 64 columns of rows g and g+8
-    z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
-    z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
-    z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
-    z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
-    F.z0 = z0 + S.b3;
-    F.z1 = z1 + S.b3;
 }
 
 __device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
@@ -464,7 +308,10 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
             tc_commit(bar);
         }
         ok = mbar_wait(bar, parity);
-        if (group_sync_or(bid, !ok)) break;
+        if (group_sync_or(bid, !ok)) {
+            ok = false;   // every thread of the group takes the failure path
+            break;
+        }
         parity ^= 1u;
         tc_fence_after();
 #pragma unroll
@@ -496,7 +343,10 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
             tc_commit(bar);
         }
         ok = mbar_wait(bar, parity);
-        if (group_sync_or(bid, !ok)) break;
+        if (group_sync_or(bid, !ok)) {
+            ok = false;   // every thread of the group takes the failure path
+            break;
+        }
         parity ^= 1u;
         tc_fence_after();
         float z = W.b3;
@@ -529,187 +379,361 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
     }
 }
 
-// Forward + backward over one mini-batch; gradients of the mean loss are
-// accumulated into grad (zeroed by the caller) and the loss into loss[0].
-__global__ void __launch_bounds__(256, 1)
-mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64_t total,
-                 int64_t first, int64_t batch, int64_t pa, int64_t pc, float* grad, float* loss)
+// ---------------------------------------------------------------------------
+// Training: fused forward + backward over one mini-batch on tcgen05.
+//
+// A CTA of four warps takes 128 mini-batch rows per tile (row t = thread t =
+// TMEM lane t), with the scoring kernel's operand layouts and rounding
+// points, and accumulates the weight gradients of all its tiles in TMEM:
+//   layer 1, layer 2      as in scoring (biases in the K padding)
+//   dz = (sigmoid(z) - y) / batch,  dh2 = dz w3 relu'(a2)          (FP32)
+//   dh1 = (dh2 W2^T) relu'(a1):  D[128 x 64] = DH2[128 x 64] W2n  (BF16 dh2)
+//   [dW2  .  ]   [h1^T]
+//   [ .  dW1 ] = [x^T ] [dh2 | dh1]: Dw[128 x 128] += A[128 x K] B[K x 128]
+// with K = the tile's 128 rows (eight MMAs of K = 16): rows 0-63 of A are
+// h1^T, rows 64-71 x^T, the rest zero; columns 0-63 of B are dh2, 64-127
+// dh1 (both BF16), so the two diagonal blocks of Dw are dW2 and dW1 and the
+// off-diagonal ones are not used. Transposed operands are written by the
+// epilogues element by element. The bias and w3 gradients are FP32 column
+// sums over the tile, staged through shared memory. Dw sits in TMEM columns
+// 128-255 and is added into the gradient once per CTA.
+
+constexpr int kKr = kTcRows;   // K of the weight-gradient GEMM: the tile's rows
+constexpr int kStage = 68;     // FP32 staging row (64 + 4: conflict-free 16-byte stores)
+constexpr uint32_t kIdescM128N128 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct TrainSmem {
+    uint16_t w1[64 * kK1];        // layer-1 B = [W1 ; b1]^T
+    uint16_t w2[64 * kK2];        // layer-2 B = [W2 ; b2]^T
+    uint16_t w2n[64 * 64];        // dh1 B = W2 as [in][out] (K = out)
+    uint16_t x[kTcRows * kK1];    // layer-1 A (16 row groups x 2 K groups; K 8-10 constant ones)
+    uint16_t h1[kTcRows * kK2];   // layer-2 A (16 x 10; K 64-66 constant ones)
+    uint16_t dh2[kTcRows * 64];   // dh1 A: dh2 [row][out]
+    uint16_t at[128 * kKr];       // weight-gradient A: [h1^T ; x^T ; 0] (16 x 16 K groups)
+    uint16_t bt[128 * kKr];       // weight-gradient B: [dh2 | dh1]^T
+    float stage[kTcRows * kStage];   // FP32 rows for the column sums
+    float w3[64];
+    float red[3 * 64 + 2];        // b1, b2, w3 gradient sums, b3 sum, loss sum
+    float b3;
+    uint32_t tmem;
+    unsigned long long bar;
+};
+static_assert(offsetof(TrainSmem, w2) % 128 == 0 && offsetof(TrainSmem, w2n) % 128 == 0 &&
+                  offsetof(TrainSmem, x) % 128 == 0 && offsetof(TrainSmem, h1) % 128 == 0 &&
+                  offsetof(TrainSmem, dh2) % 128 == 0 && offsetof(TrainSmem, at) % 128 == 0 &&
+                  offsetof(TrainSmem, bt) % 128 == 0 && offsetof(TrainSmem, stage) % 16 == 0,
+              "operand tiles must start on core-matrix boundaries");
+static_assert(sizeof(TrainSmem) <= 227 * 1024, "training CTA does not fit");
+
+// Column sums of the staged FP32 tile into red[0..63] (two threads per column).
+__device__ __forceinline__ void stage_column_sums(const float* stage, float* red, int t)
 {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    MlpSmem& S = *reinterpret_cast<MlpSmem*>(dsm);
-    uint16_t (*xs)[kPadK1] = reinterpret_cast<uint16_t (*)[kPadK1]>(dsm + kOffX);
-    uint16_t (*h1s)[kPad64] = reinterpret_cast<uint16_t (*)[kPad64]>(dsm + kOffH1);
-    uint16_t (*dh2s)[kPad64] = h1s + kBlockRows;
-    uint16_t (*dh1s)[kPad64] = dh2s + kBlockRows;
-    float* red = reinterpret_cast<float*>(dsm + kOffRed);   // b1, b2, w3 partials, then b3
-    load_weights(S, P, true);
-    for (int i = threadIdx.x; i < 3 * 64 + 1; i += blockDim.x) red[i] = 0.0f;
+    const int c = t & 63, r0 = (t >> 6) * 64;
+    float s = 0.0f;
+    for (int r = r0; r < r0 + 64; ++r) s += stage[r * kStage + c];
+    atomicAdd(&red[c], s);
+}
+
+__global__ void __launch_bounds__(kTcRows, 1)
+mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64_t total, int64_t first,
+                 int64_t batch, int64_t pa, int64_t pc, float* grad, float* loss)
+{
+    extern __shared__ __align__(128) unsigned char tsm[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(tsm);
+    const int t = threadIdx.x, warp = t >> 5;
+    for (int i = t; i < 704; i += kTcRows) {
+        const int out = i & 63;
+        if (i < 512) {   // W2^T (forward) and W2 (dh1) K group c of output / input `out`
+            const int c = i >> 6;
+            float w[8], u[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                w[j] = __ldg(P + kW2 + (c * 8 + j) * 64 + out);   // W2[in = 8c+j][out]
+                u[j] = __ldg(P + kW2 + out * 64 + c * 8 + j);     // W2[in = out][out' = 8c+j]
+            }
+            *reinterpret_cast<uint4*>(&S.w2[core_idx(out, c * 8, kK2 / 8)]) =
+                make_uint4(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]), pack_bf16(w[4], w[5]),
+                           pack_bf16(w[6], w[7]));
+            *reinterpret_cast<uint4*>(&S.w2n[core_idx(out, c * 8, 8)]) =
+                make_uint4(pack_bf16(u[0], u[1]), pack_bf16(u[2], u[3]), pack_bf16(u[4], u[5]),
+                           pack_bf16(u[6], u[7]));
+        } else if (i < 576) {
+            float w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[j] = __ldg(P + kW1 + j * 64 + out);
+            *reinterpret_cast<uint4*>(&S.w1[core_idx(out, 0, kK1 / 8)]) =
+                make_uint4(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]), pack_bf16(w[4], w[5]),
+                           pack_bf16(w[6], w[7]));
+            *reinterpret_cast<uint4*>(&S.w1[core_idx(out, 8, kK1 / 8)]) = bias_row(__ldg(P + kB1 + out), false);
+        } else if (i < 640) {
+            *reinterpret_cast<uint4*>(&S.w2[core_idx(out, 64, kK2 / 8)]) = bias_row(__ldg(P + kB2 + out), false);
+            *reinterpret_cast<uint4*>(&S.w2[core_idx(out, 72, kK2 / 8)]) = make_uint4(0u, 0u, 0u, 0u);
+        } else if (i < 704) {
+            S.w3[out] = __ldg(P + kW3 + out);
+            if (out == 0) S.b3 = __ldg(P + kB3);
+        }
+    }
+    for (int i = t; i < 3 * 64 + 2; i += kTcRows) S.red[i] = 0.0f;
+    // constant parts of the A tiles: the ones columns, and rows 72-127 of the
+    // weight-gradient A (x^T fills rows 64-71 each tile)
+    *reinterpret_cast<uint4*>(&S.x[core_idx(t, 8, kK1 / 8)]) = bias_row(0.0f, true);
+    *reinterpret_cast<uint4*>(&S.h1[core_idx(t, 64, kK2 / 8)]) = bias_row(0.0f, true);
+    *reinterpret_cast<uint4*>(&S.h1[core_idx(t, 72, kK2 / 8)]) = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = t; i < 56 * kKr / 8; i += kTcRows) {   // rows 72..127, 16 B at a time
+        const int m = 72 + i / (kKr / 8), k = (i % (kKr / 8)) * 8;
+        *reinterpret_cast<uint4*>(&S.at[core_idx(m, k, kKr / 8)]) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&S.tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's lanes, columns 0-63
+    const uint32_t dw = tmem + 128u;                                // weight-gradient accumulator
+    const uint64_t dx = smem_desc(S.x, (kK1 / 8) * 128), dw1 = smem_desc(S.w1, (kK1 / 8) * 128);
+    const uint64_t dh1a = smem_desc(S.h1, (kK2 / 8) * 128), dw2 = smem_desc(S.w2, (kK2 / 8) * 128);
+    const uint64_t ddh2 = smem_desc(S.dh2, 8 * 128), dw2n = smem_desc(S.w2n, 8 * 128);
+    const uint64_t dat = smem_desc(S.at, (kKr / 8) * 128), dbt = smem_desc(S.bt, (kKr / 8) * 128);
     const float inv_b = 1.0f / (float)batch;
-    float acc[8][4];   // warps 0-3: dW2 rows warp*16.., warp 4: dW1 (rows = features)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-    float lsum = 0.0f;
-
-    const int64_t blocks = (batch + kBlockRows - 1) / kBlockRows;
+    uint32_t parity = 0;
+    bool ok = true, any = false;
+    float dzsum = 0.0f, lsum = 0.0f;
+    const int64_t blocks = (batch + kTcRows - 1) / kTcRows;
     for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
-        const int64_t b0 = blk * kBlockRows + warp * 16 + g, b1 = b0 + 8;
-        const int64_t row0 = b0 < batch ? (int64_t)(((unsigned __int128)pa * (unsigned __int128)(first + b0) + pc) % (unsigned __int128)total) : -1;
-        const int64_t row1 = b1 < batch ? (int64_t)(((unsigned __int128)pa * (unsigned __int128)(first + b1) + pc) % (unsigned __int128)total) : -1;
-        Fwd F;
-        mlp_fwd_tile(S, feat, row0, row1, F);
-        const int lr0 = warp * 16 + g, lr1 = lr0 + 8;   // rows of the CTA block
-        // x tile for dW1 (features 0..7, 8..15 zero)
-        *reinterpret_cast<uint32_t*>(&xs[lr0][t * 2]) =
-            row0 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row0 * 8 + t * 2) : 0u;
-        *reinterpret_cast<uint32_t*>(&xs[lr1][t * 2]) =
-            row1 >= 0 ? *reinterpret_cast<const uint32_t*>(feat + row1 * 8 + t * 2) : 0u;
-        *reinterpret_cast<uint32_t*>(&xs[lr0][t * 2 + 8]) = 0u;
-        *reinterpret_cast<uint32_t*>(&xs[lr1][t * 2 + 8]) = 0u;
-        // h1 tile for dW2
+        const int64_t b = blk * kTcRows + t;
+        const bool valid = b < batch;
+        const int64_t row =
+            valid ? (int64_t)(((unsigned __int128)pa * (unsigned __int128)(first + b) + pc) % (unsigned __int128)total) : 0;
+        const uint4 xv = valid ? __ldg(reinterpret_cast<const uint4*>(feat) + row) : make_uint4(0u, 0u, 0u, 0u);
+        const float y = valid ? label[row] : 0.0f;
+        *reinterpret_cast<uint4*>(&S.x[core_idx(t, 0, kK1 / 8)]) = xv;
+        {   // x^T into rows 64-71 of the weight-gradient A
+            const uint16_t* xs = reinterpret_cast<const uint16_t*>(&xv);
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int kt = nt >> 1, hi = nt & 1;
-            *reinterpret_cast<uint32_t*>(&h1s[lr0][nt * 8 + t * 2]) = F.h1a[kt][0 + 2 * hi];
-            *reinterpret_cast<uint32_t*>(&h1s[lr1][nt * 8 + t * 2]) = F.h1a[kt][1 + 2 * hi];
+            for (int f = 0; f < 8; ++f) S.at[core_idx(64 + f, t, kKr / 8)] = xs[f];
         }
-        // dL/dz of the mean loss, and the loss itself
-        float dz0 = 0.0f, dz1 = 0.0f;
-        if (row0 >= 0) {
-            const float y = label[row0];
-            dz0 = (sigmoidf(F.z0) - y) * inv_b;
-            if (t == 0) lsum += bce_term(F.z0, y);
-        }
-        if (row1 >= 0) {
-            const float y = label[row1];
-            dz1 = (sigmoidf(F.z1) - y) * inv_b;
-            if (t == 0) lsum += bce_term(F.z1, y);
-        }
-        // dw3, db3, dh2 = dz w3 * relu'(a2), db2
-        uint32_t dh2a[4][4];
-        float pw3[16], pb2[16];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int col = nt * 8 + t * 2;
-            const float wa = S.w3[col], wb = S.w3[col + 1];
-            pw3[nt * 2] = F.h2[nt][0] * dz0 + F.h2[nt][2] * dz1;
-            pw3[nt * 2 + 1] = F.h2[nt][1] * dz0 + F.h2[nt][3] * dz1;
-            float d[4];
-            d[0] = (F.m2 >> (nt * 4 + 0)) & 1u ? dz0 * wa : 0.0f;
-            d[1] = (F.m2 >> (nt * 4 + 1)) & 1u ? dz0 * wb : 0.0f;
-            d[2] = (F.m2 >> (nt * 4 + 2)) & 1u ? dz1 * wa : 0.0f;
-            d[3] = (F.m2 >> (nt * 4 + 3)) & 1u ? dz1 * wb : 0.0f;
-            pb2[nt * 2] = d[0] + d[2];
-            pb2[nt * 2 + 1] = d[1] + d[3];
-            const int kt = nt >> 1, hi = nt & 1;
-            dh2a[kt][0 + 2 * hi] = pack_bf16(d[0], d[1]);
-            dh2a[kt][1 + 2 * hi] = pack_bf16(d[2], d[3]);
-            *reinterpret_cast<uint32_t*>(&dh2s[lr0][col]) = dh2a[kt][0 + 2 * hi];
-            *reinterpret_cast<uint32_t*>(&dh2s[lr1][col]) = dh2a[kt][1 + 2 * hi];
-        }
-        // dh1 = dh2 W2^T * relu'(a1)   (B(k=out, n=in) = W2[in][out] = w2[n][k])
-        float pb1[16];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt) {
-                const uint32_t bb0 = *reinterpret_cast<const uint32_t*>(&S.w2[nt * 8 + g][kt * 16 + t * 2]);
-                const uint32_t bb1 = *reinterpret_cast<const uint32_t*>(&S.w2[nt * 8 + g][kt * 16 + 8 + t * 2]);
-                mma16816(c, dh2a[kt], bb0, bb1);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (!((F.m1 >> (nt * 4 + i)) & 1u)) c[i] = 0.0f;
-            pb1[nt * 2] = c[0] + c[2];
-            pb1[nt * 2 + 1] = c[1] + c[3];
-            const int col = nt * 8 + t * 2;
-            *reinterpret_cast<uint32_t*>(&dh1s[lr0][col]) = pack_bf16(c[0], c[1]);
-            *reinterpret_cast<uint32_t*>(&dh1s[lr1][col]) = pack_bf16(c[2], c[3]);
-        }
-        // column sums over the 8 row groups of the warp, then into shared memory
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-#pragma unroll
-            for (int off = 4; off < 32; off <<= 1) {
-                pw3[i] += __shfl_xor_sync(0xffffffffu, pw3[i], off);
-                pb2[i] += __shfl_xor_sync(0xffffffffu, pb2[i], off);
-                pb1[i] += __shfl_xor_sync(0xffffffffu, pb1[i], off);
-            }
-        }
-        if (g == 0) {
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int col = nt * 8 + t * 2;
-                atomicAdd(&red[col], pb1[nt * 2]);
-                atomicAdd(&red[col + 1], pb1[nt * 2 + 1]);
-                atomicAdd(&red[64 + col], pb2[nt * 2]);
-                atomicAdd(&red[64 + col + 1], pb2[nt * 2 + 1]);
-                atomicAdd(&red[128 + col], pw3[nt * 2]);
-                atomicAdd(&red[128 + col + 1], pw3[nt * 2 + 1]);
-            }
-        }
-        float dzs = dz0 + dz1;
-#pragma unroll
-        for (int off = 4; off < 32; off <<= 1) dzs += __shfl_xor_sync(0xffffffffu, dzs, off);
-        if (lane == 0) atomicAdd(&red[192], dzs);
+        // ---- layer 1
+        fence_async_smem();
+        tc_fence_before();
         __syncthreads();
-        // weight gradients over the block's 128 rows (K = rows):
-        //   warps 0-3: dW2[in = warp*16 ..][out] = sum_r h1[r][in] dh2[r][out]
-        //   warp 4:    dW1[f][in]              = sum_r x[r][f]  dh1[r][in]
-        if (warp < 5) {
-            uint16_t (*As)[kPad64] = h1s;
-            uint16_t (*Bs)[kPad64] = warp < 4 ? dh2s : dh1s;
-            const int m0 = warp < 4 ? warp * 16 : 0;
-            const int q = lane >> 3, r8 = lane & 7;
-#pragma unroll 1
-            for (int k0 = 0; k0 < kBlockRows; k0 += 16) {
-                uint32_t af[4];
-                const int arow = k0 + r8 + ((q & 2) ? 8 : 0), acol = m0 + ((q & 1) ? 8 : 0);
-                if (warp < 4) ldsm_x4_trans(af, &As[arow][acol]);
-                else ldsm_x4_trans(af, &xs[arow][acol]);
+        if (t == 0) {
+            tc_fence_after();
+            tc_mma(tmem, dx, dw1, kIdescM128N64, 0u);
+            tc_commit(bar);
+        }
+        ok = mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            ok = false;   // every thread takes the failure path
+            break;
+        }
+        parity ^= 1u;
+        tc_fence_after();
+        uint32_t m1[2] = {0u, 0u};   // relu'(a1)
 #pragma unroll
-                for (int np = 0; np < 4; ++np) {
-                    uint32_t bf[4];
-                    const int brow = k0 + r8 + ((q & 1) ? 8 : 0), bcol = np * 16 + ((q & 2) ? 8 : 0);
-                    ldsm_x4_trans(bf, &Bs[brow][bcol]);
-                    mma16816(acc[np * 2], af, bf[0], bf[1]);
-                    mma16816(acc[np * 2 + 1], af, bf[2], bf[3]);
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tc_ld32(lanes + 32 * half, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t q[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = c * 8 + 2 * j;
+                    q[j] = pack_bf16(fmaxf(v[k], 0.0f), fmaxf(v[k + 1], 0.0f));
+                }
+                *reinterpret_cast<uint4*>(&S.h1[core_idx(t, (half * 4 + c) * 8, kK2 / 8)]) =
+                    make_uint4(q[0], q[1], q[2], q[3]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {   // h1^T into rows 0-63 of the weight-gradient A
+                    const int in = half * 32 + c * 8 + 2 * j;
+                    S.at[core_idx(in, t, kKr / 8)] = (uint16_t)(q[j] & 0xFFFFu);
+                    S.at[core_idx(in + 1, t, kKr / 8)] = (uint16_t)(q[j] >> 16);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                if (v[k] > 0.0f) m1[half] |= 1u << k;
+        }
+        // ---- layer 2
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < kK2 / 16; ++kk)
+                tc_mma(tmem, dh1a + 16u * kk, dw2 + 16u * kk, kIdescM128N64, kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+        }
+        ok = mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            ok = false;   // every thread takes the failure path
+            break;
+        }
+        parity ^= 1u;
+        tc_fence_after();
+        float a2[64];
+        tc_ld32(lanes, a2);
+        tc_ld32(lanes + 32, a2 + 32);
+        tc_wait_ld();
+        float z = S.b3;   // as in scoring
+#pragma unroll
+        for (int c = 0; c < 64; ++c) z = __fmaf_rn(fmaxf(a2[c], 0.0f), S.w3[c], z);
+        const float dz = valid ? (sigmoidf(z) - y) * inv_b : 0.0f;
+        if (valid) lsum += bce_term(z, y);
+        dzsum += dz;
+        // dw3 partials: h2 dz, staged for the column sums
+#pragma unroll
+        for (int c = 0; c < 64; c += 4)
+            *reinterpret_cast<float4*>(&S.stage[t * kStage + c]) =
+                make_float4(fmaxf(a2[c], 0.0f) * dz, fmaxf(a2[c + 1], 0.0f) * dz, fmaxf(a2[c + 2], 0.0f) * dz,
+                            fmaxf(a2[c + 3], 0.0f) * dz);
+        __syncthreads();
+        stage_column_sums(S.stage, S.red + 128, t);
+        __syncthreads();
+        // dh2 = dz w3 relu'(a2): FP32 staged for db2; BF16 as the dh1 A and
+        // as columns 0-63 of the weight-gradient B
+#pragma unroll
+        for (int c = 0; c < 64; ++c) a2[c] = a2[c] > 0.0f ? dz * S.w3[c] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 64; c += 4)
+            *reinterpret_cast<float4*>(&S.stage[t * kStage + c]) = make_float4(a2[c], a2[c + 1], a2[c + 2], a2[c + 3]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint32_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = pack_bf16(a2[c * 8 + 2 * j], a2[c * 8 + 2 * j + 1]);
+            *reinterpret_cast<uint4*>(&S.dh2[core_idx(t, c * 8, 8)]) = make_uint4(q[0], q[1], q[2], q[3]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int out = c * 8 + 2 * j;
+                S.bt[core_idx(out, t, kKr / 8)] = (uint16_t)(q[j] & 0xFFFFu);
+                S.bt[core_idx(out + 1, t, kKr / 8)] = (uint16_t)(q[j] >> 16);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // ---- dh1 = dh2 W2^T (the tensor core) while the db2 sums run
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc_mma(tmem, ddh2 + 16u * kk, dw2n + 16u * kk, kIdescM128N64, kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+        }
+        stage_column_sums(S.stage, S.red + 64, t);
+        ok = mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            ok = false;   // every thread takes the failure path
+            break;
+        }
+        parity ^= 1u;
+        tc_fence_after();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tc_ld32(lanes + 32 * half, v);
+            tc_wait_ld();
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                if (!((m1[half] >> k) & 1u)) v[k] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 32; c += 4)
+                *reinterpret_cast<float4*>(&S.stage[t * kStage + half * 32 + c]) =
+                    make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {   // dh1 as columns 64-127 of the weight-gradient B
+                const uint32_t q = pack_bf16(v[2 * j], v[2 * j + 1]);
+                const int in = half * 32 + 2 * j;
+                S.bt[core_idx(64 + in, t, kKr / 8)] = (uint16_t)(q & 0xFFFFu);
+                S.bt[core_idx(64 + in + 1, t, kKr / 8)] = (uint16_t)(q >> 16);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // ---- weight gradients, accumulated over the CTA's tiles
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < kKr / 16; ++kk)
+                tc_mma(dw, dat + 16u * kk, dbt + 16u * kk, kIdescM128N128, (any || kk > 0) ? 1u : 0u);
+            tc_commit(bar);
+        }
+        any = true;
+        stage_column_sums(S.stage, S.red, t);   // db1
+        ok = mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            ok = false;   // every thread takes the failure path
+            break;
+        }
+        parity ^= 1u;
+        tc_fence_after();
+    }
+    if (!ok) {
+        // a wait gave up: one more bounded wait for the MMA in flight; the
+        // loss becomes NaN and no gradient is added
+        mbar_wait(bar, parity);
+        if (t == 0) atomicAdd(loss, __int_as_float(0x7fc00000));
+    } else {
+        if (any) {   // Dw rows: 0-63 dW2[in][out] (columns 0-63), 64-71 dW1[f][h] (columns 64-127)
+            const int m = warp * 32 + (t & 31);
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                float v[32];
+                tc_ld32(dw + ((uint32_t)(warp * 32) << 16) + 32 * q, v);
+                tc_wait_ld();
+                if (m < 64 && q < 2) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) atomicAdd(&grad[kW2 + m * 64 + q * 32 + c], v[c]);
+                } else if (m >= 64 && m < 72 && q >= 2) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) atomicAdd(&grad[kW1 + (m - 64) * 64 + (q - 2) * 32 + c], v[c]);
                 }
             }
         }
+        // dz and loss sums of the CTA
+        float l = lsum, d = dzsum;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            l += __shfl_xor_sync(0xffffffffu, l, off);
+            d += __shfl_xor_sync(0xffffffffu, d, off);
+        }
+        if ((t & 31) == 0) {
+            atomicAdd(&S.red[192], d);
+            atomicAdd(&S.red[193], l);
+        }
         __syncthreads();
-    }
-    // flush the CTA's partial gradients
-    if (warp < 4) {
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int in0 = warp * 16 + g, out = nt * 8 + t * 2;
-            atomicAdd(&grad[kW2 + in0 * 64 + out], acc[nt][0]);
-            atomicAdd(&grad[kW2 + in0 * 64 + out + 1], acc[nt][1]);
-            atomicAdd(&grad[kW2 + (in0 + 8) * 64 + out], acc[nt][2]);
-            atomicAdd(&grad[kW2 + (in0 + 8) * 64 + out + 1], acc[nt][3]);
+        if (t < 64) {
+            atomicAdd(&grad[kB1 + t], S.red[t]);
+            atomicAdd(&grad[kB2 + t], S.red[64 + t]);
+            atomicAdd(&grad[kW3 + t], S.red[128 + t]);
         }
-    } else if (warp == 4) {
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int out = nt * 8 + t * 2;   // rows g < 8 are the real features
-            atomicAdd(&grad[kW1 + g * 64 + out], acc[nt][0]);
-            atomicAdd(&grad[kW1 + g * 64 + out + 1], acc[nt][1]);
+        if (t == 0) {
+            atomicAdd(&grad[kB3], S.red[192]);
+            atomicAdd(loss, S.red[193] * inv_b);
         }
     }
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-        atomicAdd(&grad[kB1 + i], red[i]);
-        atomicAdd(&grad[kB2 + i], red[64 + i]);
-        atomicAdd(&grad[kW3 + i], red[128 + i]);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256u) : "memory");
     }
-    if (threadIdx.x == 0) atomicAdd(&grad[kB3], red[192]);
-    float l = lsum;   // non-zero on lanes t == 0 only
-#pragma unroll
-    for (int off = 4; off < 32; off <<= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
-    if (lane == 0) atomicAdd(loss, l * inv_b);
 }
 
 __global__ void adam_kernel(float* P, const float* G, float* M, float* Vv, int n, float lr, float b1,
@@ -900,22 +924,22 @@ acs_status acs_mlp_train_batch(const float* dev_params, const uint16_t* dev_feat
                                float* dev_grad, float* dev_loss, void* stream)
 {
     if (!dev_params || !dev_feat || !dev_label || !dev_grad || !dev_loss || total < 1 || batch < 1 ||
-        first < 0 || perm_a < 1 || perm_c < 0)
+        first < 0 || perm_a < 1 || perm_c < 0 || ((uintptr_t)dev_feat & 15))
         return ACS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(dev_grad, 0, sizeof(float) * ACS_MLP_PARAMS, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dev_loss, 0, sizeof(float), st);
-    const size_t smem = kTrainSmem;
+    const size_t smem = sizeof(TrainSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return ACS_ECUDA;
-    const int64_t blocks = (batch + kBlockRows - 1) / kBlockRows;
+    const int64_t blocks = (batch + kTcRows - 1) / kTcRows;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)(blocks < sms ? blocks : sms);
-    mlp_train_kernel<<<grid, 256, smem, st>>>(dev_params, dev_feat, dev_label, total, first, batch, perm_a,
-                                              perm_c, dev_grad, dev_loss);
+    mlp_train_kernel<<<grid, kTcRows, smem, st>>>(dev_params, dev_feat, dev_label, total, first, batch,
+                                                  perm_a, perm_c, dev_grad, dev_loss);
     return launched(cudaGetLastError());
 }
 

@@ -128,6 +128,7 @@ def test_prior_calls_reject_bad_arguments_on_host(lib):
     assert lib.acs_mlp_train_batch(fake, fake, fake, 10, 0, 0, 1, 0, fake, fake, None) == E
     assert lib.acs_mlp_train_batch(fake, fake, fake, 10, 0, 4, 0, 0, fake, fake, None) == E
     assert lib.acs_mlp_train_batch(fake, fake, None, 10, 0, 4, 1, 0, fake, fake, None) == E
+    assert lib.acs_mlp_train_batch(fake, vp(0x1008), fake, 10, 0, 4, 1, 0, fake, fake, None) == E
     assert lib.acs_mlp_adam(fake, fake, fake, fake, 0, 1e-3, 0.9, 0.999, 1e-8, None) == E
     assert lib.acs_mlp_adam(None, fake, fake, fake, 1, 1e-3, 0.9, 0.999, 1e-8, None) == E
     assert lib.acs_kernel_mode(None) == -1
