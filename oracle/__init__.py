@@ -96,6 +96,8 @@ def lib():
         L.acsref_create_tables.restype = ctypes.c_int
         L.acsref_run.argtypes = [_vp, _i32]
         L.acsref_run.restype = ctypes.c_int
+        L.acsref_local_step.argtypes = [_vp, _P(np.int32), _P(np.int32)]
+        L.acsref_local_step.restype = ctypes.c_int
         L.acsref_get_tours.argtypes = [_vp, _P(np.int32), _P(np.int64)]
         L.acsref_best.argtypes = [_vp, _P(np.int32), ctypes.POINTER(_i64)]
         L.acsref_best.restype = ctypes.c_int
@@ -213,6 +215,13 @@ class Colony:
         rc = lib().acsref_run(self._h, iters)
         if rc != 0:
             raise OracleError("acsref_run failed with status %d" % rc)
+
+    def local_step(self, frm, to):
+        """Apply the local updates of one synchronous step (ant a took frm[a] -> to[a])."""
+        rc = lib().acsref_local_step(self._h, np.ascontiguousarray(frm, np.int32),
+                                     np.ascontiguousarray(to, np.int32))
+        if rc != 0:
+            raise OracleError("bad step")
 
     @property
     def iteration(self):

@@ -506,6 +506,16 @@ static void local_update_step(acsref_colony* C, const int32_t* from, const int32
     }
 }
 
+int acsref_local_step(acsref_colony* C, const int32_t* from, const int32_t* to)
+{
+    if (!C || !from || !to) return 1;
+    for (int32_t a = 0; a < C->m; a++)
+        if (from[a] < 0 || from[a] >= C->n || to[a] < 0 || to[a] >= C->n || from[a] == to[a])
+            return 1;
+    local_update_step(C, from, to);
+    return 0;
+}
+
 static void one_iteration(acsref_colony* C)
 {
     const int32_t n = C->n, m = C->m;

@@ -62,6 +62,13 @@ int     acsref_create_tables(const int32_t* xy, int32_t n, const int32_t* nn,
                              const float* w, int32_t cl, const acsref_params* p,
                              int32_t instance, acsref_colony** out);
 int     acsref_run(acsref_colony* c, int32_t iters);
+/* The local updates of ONE synchronous step (Alg. 1, Eq. 3 folded over the
+ * ants that share an undirected edge; Alg. 3 on the SPM), applied to the
+ * colony's pheromone memory exactly as a run applies them: from[a] -> to[a]
+ * (m entries) is the edge ant a took. Exposed so tests can pin the order and
+ * multiplicity rules on hand-made steps. Returns 0, or 1 for a node out of
+ * range or a self-loop (nothing changed). */
+int     acsref_local_step(acsref_colony* c, const int32_t* from, const int32_t* to);
 int     acsref_get_tours(const acsref_colony* c, int32_t* tours, int64_t* lens);
 int     acsref_best(const acsref_colony* c, int32_t* tour, int64_t* len);
 /* Offer a tour from elsewhere (another colony: multi-colony exchange). It

@@ -247,6 +247,104 @@ def test_spm_hand_trace(oracle_mod):
     assert int(hits[0]) == 2 and int(misses[0]) == 5
 
 
+def _parse_step_trace(path):
+    steps = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("step"):
+            edges = [tuple(int(x) for x in e.split(">")) for e in line.split(":", 1)[1].split()]
+            steps.append({"edges": edges, "recs": {}, "count": None})
+        elif line.startswith("rec"):
+            head, idx, tail, val = [f.split() for f in line.split("|")]
+            steps[-1]["recs"][int(head[1])] = ([int(x) for x in idx], int(tail[0]), val)
+        elif line.startswith("count"):
+            f = line.split()
+            steps[-1]["count"] = (int(f[2]), int(f[4]))
+    return steps
+
+
+def test_spm_step_event_order_hand_trace(oracle_mod):
+    # the order of the SPM events inside one synchronous step (lowest ant
+    # first, the ant's own direction) and the folding of an edge taken by
+    # several ants into one event per record decide which trails a record
+    # evicts: pinned against a hand trace of two steps on five records
+    xy = np.array([[0, 0], [100, 0], [0, 100], [100, 100], [50, 300]], np.int32)
+    c = oracle.Colony(xy, oracle.make_params(m=4, cl=4, memory=1, spm_slots=2))
+    steps = _parse_step_trace(os.path.join(GOLDEN, "spm_step_order.txt"))
+    assert len(steps) == 2
+    for st in steps:
+        frm = [a for a, _ in st["edges"]]
+        to = [b for _, b in st["edges"]]
+        c.local_step(frm, to)
+        val, idx, tail = c.pheromone()
+        for r, (want_idx, want_tail, want_val) in st["recs"].items():
+            assert list(idx[r]) == want_idx, (r, idx[r])
+            assert int(tail[r]) == want_tail, (r, tail[r])
+            for got, w in zip(val[r], want_val):
+                assert got == (c.tau0 if w == "t0" else np.float32(w)), (r, val[r])
+        fb, sel, hits, misses = c.stats()
+        assert (hits, misses) == st["count"]
+
+
+def test_opposite_directions_in_one_step_are_one_update(oracle_mod):
+    # two ants crossing the same undirected edge {a,b} in opposite directions
+    # in one step give ONE folded update tau0 + P[2]*(tau - tau0) (Eq. 3 applied
+    # twice in closed form), written to both matrix halves; counting a->b and
+    # b->a as two edges would compose two single updates instead, which lands
+    # on a different FP32 value for the trail used here
+    xy = instances.uniform(9, side=1000, seed=21)
+    c = oracle.Colony(xy, oracle.make_params(m=3, cl=8, q0=0.9, xi=0.1, rho=0.1))
+    tau0 = np.float32(c.tau0)
+    f = np.float32(1.0) - np.float32(0.1)
+    P1 = f
+    P2 = np.float32(f * f)
+
+    def fold(t, P):
+        return np.float32(tau0 + np.float32(P * np.float32(t - tau0)))
+
+    # run until some edge of the best tour holds a trail on which the folded
+    # value, the composition of two single updates and a lost update (both
+    # ants starting from the old trail) are three different FP32 numbers
+    for _ in range(40):
+        c.run(1)   # the global update leaves the best tour's edges above tau0
+        best, _ = c.best()
+        tau = c.pheromone()
+        sep = [i for i in range(9)
+               if len({float(fold(tau[best[i], best[(i + 1) % 9]], P2)),
+                       float(fold(fold(tau[best[i], best[(i + 1) % 9]], P1), P1)),
+                       float(fold(tau[best[i], best[(i + 1) % 9]], P1))}) == 3]
+        if sep:
+            break
+    assert sep, "no trail separates the readings"
+    i = sep[0]
+    a, b = int(best[i]), int(best[(i + 1) % 9])
+    x, y = int(best[(i + 4) % 9]), int(best[(i + 5) % 9])
+    t = np.float32(tau[a, b])
+    assert t > tau0
+    want = fold(t, P2)
+    tx = np.float32(tau[x, y])
+    c.local_step([a, b, x], [b, a, y])
+    tau2 = c.pheromone()
+    assert tau2[a, b] == want and tau2[b, a] == want
+    assert tau2[x, y] == fold(tx, P1)
+    # nothing else moved
+    mask = np.ones_like(tau, bool)
+    for u, v in ((a, b), (b, a), (x, y), (y, x)):
+        mask[u, v] = False
+    assert np.array_equal(tau[mask].view(np.uint32), tau2[mask].view(np.uint32))
+
+
+def test_local_step_rejects_bad_edges(oracle_mod):
+    xy = instances.uniform(6, side=1000, seed=3)
+    c = oracle.Colony(xy, oracle.make_params(m=2, cl=5))
+    with pytest.raises(oracle.OracleError):
+        c.local_step([0, 1], [0, 2])
+    with pytest.raises(oracle.OracleError):
+        c.local_step([0, 1], [6, 2])
+
+
 # ---------------------------------------------------------------- colony
 def _check_tours(xy, tours, lens):
     D = _np_dist(xy)
