@@ -203,6 +203,31 @@ def rank_seed(rank):
     return {"instances_seed_offset": rank, "philox_seed": 1 + rank}
 
 
+# Batched workloads shard by instance across ranks (LPT on m*(n-1), global
+# instance ids, no collective); the single-instance ones run one replica per
+# rank with its own seed.
+SHARDED = ("batch256", "large16")
+
+
+def rank_share(rank, world):
+    """This rank's instances: (global ids or None, coords, offsets, sizes,
+    philox seed, sizes of every instance the whole job runs, scaling)."""
+    from paper_1605_02669_gb300 import shard
+
+    if WORKLOAD in SHARDED and world > 1:
+        coords = make_coords()
+        ids, xy, off = shard.shard_of(coords, rank, world, M)
+        sizes = [coords[b].shape[0] for b in ids]
+        return ids, xy, off, sizes, 1, [c.shape[0] for c in coords], "strong"
+    rs = rank_seed(rank)
+    coords = make_coords(seed_offset=rs["instances_seed_offset"])
+    xy = np.concatenate(coords).astype(np.int32)
+    off = np.zeros(len(coords) + 1, np.int64)
+    off[1:] = np.cumsum([c.shape[0] for c in coords])
+    sizes = [c.shape[0] for c in coords]
+    return None, xy, off, sizes, rs["philox_seed"], sizes * world, "weak"
+
+
 def max_over_ranks(x, world, device):
     """The job's time is the slowest rank's."""
     if world <= 1:
@@ -458,7 +483,7 @@ def prior_scoring_leg(steps, warmup):
             "data": "synthetic N(0,1) features rounded to BF16, random N(0,0.2) weights"}
 
 
-def relaxed_leg(xy, off, steps, warmup):
+def relaxed_leg(xy, off, sizes, steps, warmup):
     """The relaxed construction (ACS-GPU-Alt, Sec. 3.1.2) on the same instances,
     pheromone matrix: no step barrier, racy local updates (not bit-exact),
     evaluation and global update in a second kernel. Timed like the main line."""
@@ -483,8 +508,8 @@ def relaxed_leg(xy, off, steps, warmup):
         e1.record(st)
         e1.synchronize()
         total += e0.elapsed_time(e1)
-    units = sum(M * (n - 1) for n in SIZES) * steps
-    best = [int(col.best(b)[1]) for b in range(len(SIZES))]
+    units = sum(M * (n - 1) for n in sizes) * steps
+    best = [int(col.best(b)[1]) for b in range(len(sizes))]
     col.close()
     return {"value": units / (total / 1000.0), "unit": "ant-steps/s",
             "ms_per_iteration": total / steps, "memory": "matrix", "best_len": best,
@@ -501,21 +526,17 @@ def run_ours(args, rank, world, local):
     import __graft_entry__
 
     __graft_entry__.build()
-    rs = rank_seed(rank)
-    coords = make_coords(seed_offset=rs["instances_seed_offset"])
-    xy = np.concatenate(coords).astype(np.int32)
-    off = np.zeros(len(coords) + 1, np.int64)
-    off[1:] = np.cumsum([c.shape[0] for c in coords])
+    ids, xy, off, sizes, seed, job_sizes, scaling = rank_share(rank, world)
     sA = torch.cuda.Stream()
     sB = torch.cuda.Stream()
     ctxs = []
     tuning = {}
     mems = {"both": WORKLOADS[WORKLOAD]["memories"], "matrix": (acs.ACS_MEM_MATRIX,),
             "spm": (acs.ACS_MEM_SPM,)}[args.only]
-    for mem, st in zip(mems, (sA, sB)):
+    for mem, st in zip(mems if sizes else (), (sA, sB)):
         p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
-                       seed=rs["philox_seed"])
-        col = acs.Colony(xy, p, offsets=off)
+                       seed=seed)
+        col = acs.Colony(xy, p, offsets=off, instance_ids=ids)
         col.set_stream(st.cuda_stream)
         if args.tpa or args.cluster:
             if args.cluster:
@@ -556,8 +577,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         step()
     torch.cuda.synchronize()
-    fb0 = [[c.stats(b)[0] for b in range(len(SIZES))] for c, _ in ctxs]
-    units_per_step = sum(M * (n - 1) for n in SIZES) * len(ctxs)
+    fb0 = [[c.stats(b)[0] for b in range(len(sizes))] for c, _ in ctxs]
     if world > 1:
         import torch.distributed as dist
 
@@ -581,8 +601,10 @@ def run_ours(args, rank, world, local):
     step_ms = [e0.elapsed_time(e1) for e0, e1, _ in events]
     kern_ms = [[k0.elapsed_time(k1) for k0, k1 in kev] for _, _, kev in events]
     total_ms = max_over_ranks(float(sum(step_ms)), world, "cuda")
-    fb1 = [[c.stats(b)[0] for b in range(len(SIZES))] for c, _ in ctxs]
-    value = job_throughput(units_per_step * args.steps, world, total_ms)
+    fb1 = [[c.stats(b)[0] for b in range(len(sizes))] for c, _ in ctxs]
+    # whole-job units: every rank's replica, or the whole sharded batch
+    job_units_per_step = len(mems) * sum(M * (n - 1) for n in job_sizes)
+    value = job_units_per_step * args.steps / (total_ms / 1000.0)
 
     # roofline of each colony's construct launch (both instances in one launch);
     # the dominant kernel is the one with the longer average launch
@@ -592,7 +614,7 @@ def run_ours(args, rank, world, local):
     for i, (col, _) in enumerate(ctxs):
         spm = col.p.memory == acs.ACS_MEM_SPM
         fb = [(b - a) / args.steps for a, b in zip(fb0[i], fb1[i])]
-        bytes_launch = sum(algorithmic_bytes(n, M, f, spm) for n, f in zip(SIZES, fb))
+        bytes_launch = sum(algorithmic_bytes(n, M, f, spm) for n, f in zip(sizes, fb))
         avg_s = float(np.mean([k[i] for k in kern_ms])) / 1000.0
         achieved = bytes_launch / avg_s / 1e9
         name = MEM_NAMES[col.p.memory]
@@ -602,11 +624,11 @@ def run_ours(args, rank, world, local):
             "frac": achieved / peak,
             "traffic": kernel_traffic(name, t["threads_per_ant"], t["cluster_size"]),
             "kernel": "construct_kernel<%d,%d> (%s, %d instances in one launch, clusters of %d)"
-                      % (t["threads_per_ant"], col.kernel_mode, name, len(SIZES),
+                      % (t["threads_per_ant"], col.kernel_mode, name, len(sizes),
                          t["cluster_size"]),
             "peak_kind": peak_kind, "kernel_ms": 1000.0 * avg_s,
             "algorithmic_bytes_per_launch": bytes_launch,
-            "fallback_rate": float(sum(fb) / (M * sum(n - 1 for n in SIZES))),
+            "fallback_rate": float(sum(fb) / (M * sum(n - 1 for n in sizes))),
         })
     roofs.sort(key=lambda r: -r["kernel_ms"])
 
@@ -619,19 +641,20 @@ def run_ours(args, rank, world, local):
         cols = []
         for mem in WORKLOADS[WORKLOAD]["memories"]:
             p = acs.params(m=M, cl=CL, memory=mem, spm_slots=8, seed=1)
-            cols.append(acs.Colony(xy, p, offsets=off))
+            cols.append(acs.Colony(xy, p, offsets=off, instance_ids=ids))
         d2h = 0
         for _ in range(args.steps):
             for c in cols:
                 c.run(1)
             for c in cols:
-                for b in range(len(SIZES)):
+                for b in range(len(sizes)):
                     t, L = c.best(b)
                     d2h += t.nbytes + 8
         t1 = time.perf_counter()
         for c in cols:
             c.close()
-        e2e = {"value": ant_steps_per_iter() * args.steps / (t1 - t0), "unit": "ant-steps/s",
+        e2e = {"value": len(WORKLOADS[WORKLOAD]["memories"]) * sum(M * (n - 1) for n in sizes)
+                        * args.steps / (t1 - t0), "unit": "ant-steps/s",
                "h2d_bytes_per_step": int(2 * xy.nbytes / args.steps + 2 * off.nbytes / args.steps),
                "d2h_bytes_per_step": int(d2h / args.steps),
                "includes": "context creation from host coordinates (candidate lists, "
@@ -641,7 +664,7 @@ def run_ours(args, rank, world, local):
     if rank != 0:
         return None
     gap = None if (args.no_gap or WORKLOAD != "paper") else gap_leg(args.gap_iters)
-    relaxed = None if args.no_relaxed else relaxed_leg(xy, off, args.steps, args.warmup)
+    relaxed = None if args.no_relaxed else relaxed_leg(xy, off, sizes, args.steps, args.warmup)
     scoring = None if args.no_prior_scoring else prior_scoring_leg(args.steps, args.warmup)
     cpu = None if args.no_cpu_baseline else cpu_baseline_leg()
     return {
@@ -653,11 +676,13 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": scaling,
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": workload_config(),
+        "config": dict(workload_config(), parallelism=(
+            "instances sharded by LPT over %d ranks" % world if scaling == "strong"
+            else "one replica per rank" if world > 1 else "one GPU")),
         "iterations_per_s": 1000.0 * args.steps / total_ms,
         "roofline": roofs[0],
         "roofline_other": roofs[1:],

@@ -110,6 +110,17 @@ acs_status acs_create(const int32_t* coords, int32_t n, const acs_params* p,
 acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets,
                             int32_t B, const acs_params* p, acs_ctx** out);
 
+/* acs_create_batch with the Philox counter word 3 of each instance given by
+ * the caller: instance_ids host int32 [B], each >= 0 (NULL = 0..B-1). An
+ * instance's random stream, and so its tours and pheromone state, depend only
+ * on its coordinates, the parameters, the seed and its id, not on which
+ * batch, context or GPU runs it: a batch split across GPUs by instance (with
+ * global ids) gives every instance the result it has in the whole batch.
+ * ACS_EINVAL for a negative id; otherwise as acs_create_batch. */
+acs_status acs_create_batch_ids(const int32_t* coords, const int64_t* offsets,
+                                const int32_t* instance_ids, int32_t B,
+                                const acs_params* p, acs_ctx** out);
+
 /* Run later work on this CUDA stream (a cudaStream_t; NULL = legacy default).
  * The CUDA graph captured for one iteration is rebuilt on the next run. */
 acs_status acs_set_stream(acs_ctx* ctx, void* cuda_stream);
@@ -156,9 +167,6 @@ int32_t acs_kernel_mode(const acs_ctx* ctx);
 acs_status acs_autotune(acs_ctx* ctx, int32_t trial_iters, int32_t* chosen_tpa,
                         int32_t* chosen_csize);
 
-/* Best-so-far tour (n node indices, 0-based, starting at the ant's first
- * node, closing implicitly) and its length. ACS_ESTATE before the first
- * iteration. */
 /* Multi-colony exchange (the paper's related work, Sec. 2; no counterpart in
  * its algorithms): offer `tour` (host int32 [n], a permutation of the
  * instance's nodes) as the best-so-far of `instance`. Its length is computed
@@ -169,6 +177,9 @@ acs_status acs_autotune(acs_ctx* ctx, int32_t trial_iters, int32_t* chosen_tpa,
 acs_status acs_offer_best_tour(acs_ctx* ctx, int32_t instance, const int32_t* tour,
                                int64_t* len_out);
 
+/* Best-so-far tour (n node indices, 0-based, starting at the ant's first
+ * node, closing implicitly) and its length. ACS_ESTATE before the first
+ * iteration (unless acs_set_state restored a best-so-far tour). */
 acs_status acs_best_tour(acs_ctx* ctx, int32_t instance, int32_t* tour_out,
                          int64_t* len_out);
 
@@ -193,7 +204,33 @@ acs_status acs_get_setup(acs_ctx* ctx, int32_t instance, int32_t* nn, float* w,
  * out[2] SPM hits, out[3] SPM misses (Sec. 3.2, Fig. spm-hit-ratio). */
 acs_status acs_get_stats(acs_ctx* ctx, int32_t instance, int64_t out[4]);
 
-/* Iterations completed (same for every instance of the context). */
+/* Checkpoint and resume of one instance: the loop state that Alg. 1 carries
+ * from one iteration to the next -- the pheromone memory (matrix, or the SPM
+ * records of Sec. 3.2 / Alg. 3), the best-so-far tour and its length L_gb,
+ * the iteration counter (Philox counter word 0 of the next iteration), the
+ * candidate rows in use (a learned prior may have rewritten them) and the
+ * counters of acs_get_stats. The tours of the last iteration are not part of
+ * it. The buffer is caller-allocated HOST memory of acs_state_size bytes, an
+ * opaque little-endian image (a 128-byte header, then the rows, the best
+ * tour and the pheromone arrays).
+ *   acs_state_size: bytes of instance's state (no device work).
+ *   acs_get_state:  synchronises the context's stream, writes the image.
+ *   acs_set_state:  replaces the instance's state with the image, after
+ *                   checking on the host that it was written for the same
+ *                   instance (n and tau0, i.e. the same coordinates) and the
+ *                   same parameters except the seed, and that every index is
+ *                   in range and the best tour is a permutation; ACS_EINVAL
+ *                   (nothing changed) otherwise, or when bytes is too small.
+ * With the same seed, running k iterations, saving, restoring into a fresh
+ * context of the same instance and running the rest is bit-identical to the
+ * unsplit run. acs_iteration reports instance 0's counter, so restoring
+ * instance 0 sets it. */
+acs_status acs_state_size(const acs_ctx* ctx, int32_t instance, int64_t* bytes);
+acs_status acs_get_state(acs_ctx* ctx, int32_t instance, void* buf, int64_t bytes);
+acs_status acs_set_state(acs_ctx* ctx, int32_t instance, const void* buf, int64_t bytes);
+
+/* Iterations completed by instance 0 (every instance of a context runs the
+ * same number of iterations; acs_set_state may restore another counter). */
 int64_t acs_iteration(const acs_ctx* ctx);
 int32_t acs_num_instances(const acs_ctx* ctx);
 int32_t acs_instance_size(const acs_ctx* ctx, int32_t instance);
@@ -204,10 +241,10 @@ int64_t acs_last_launch_count(const acs_ctx* ctx);
 /* No-allocation variant of one iteration (the paper has no counterpart; it
  * exists for callers that cannot allocate device memory, such as code running
  * inside a memory arena or pool it does not own, or a hot path where
- * cudaMalloc is not allowed). It runs exactly one iteration of Alg. 1 -- the
- * same construct kernel and the same results as acs_run_iterations on an
- * acs_create context -- on one instance whose state lives entirely in
- * caller-owned DEVICE buffers, FP32 matrix memory only, Philox instance
+ * cudaMalloc is not allowed). It runs the same iteration as
+ * acs_run_iterations(ctx, 1) on an acs_create context -- the same construct
+ * kernel and the same results -- on one instance whose state lives entirely
+ * in caller-owned DEVICE buffers, FP32 matrix memory only, Philox instance
  * index 0:
  *   dev_coords   int32 [n][2] node coordinates (input)
  *   dev_nn32     int32 [n][32] candidate lists padded with -1 (input)

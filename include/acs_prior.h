@@ -64,7 +64,9 @@ acs_status acs_prior_count_best_edges(acs_ctx* ctx, int32_t instance, float* dev
 /* Scores p = sigmoid(z) of `rows` feature rows (dev_feat [rows][8] BF16,
  * 16-byte aligned, else ACS_EINVAL) into dev_p [rows] FP32. The kernel's
  * only wait (for the tensor core's completion signal) is bounded; if it ever
- * gives up, the rows that were not scored hold NaN. */
+ * gives up, the rows that were not scored hold NaN, the device status word
+ * records it (acs_mlp_sync then returns ACS_ETIMEOUT) and tensor memory is
+ * freed only after the MMA already issued has completed. */
 acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, int64_t rows,
                            float* dev_p, void* stream);
 
@@ -73,11 +75,31 @@ acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, in
  * (perm_a coprime with total). Writes the mean BCE loss to dev_loss[0] and
  * the gradient of that mean to dev_grad [ACS_MLP_PARAMS] (both overwritten).
  * dev_feat 16-byte aligned. If a bounded wait for the tensor core gives up,
- * the loss is NaN and the gradient incomplete. */
+ * the loss is NaN, the gradient incomplete and acs_mlp_sync reports
+ * ACS_ETIMEOUT. */
 acs_status acs_mlp_train_batch(const float* dev_params, const uint16_t* dev_feat,
                                const float* dev_label, int64_t total, int64_t first,
                                int64_t batch, int64_t perm_a, int64_t perm_c, float* dev_grad,
                                float* dev_loss, void* stream);
+
+/* Waits for the work queued on `stream`, then reports whether a bounded
+ * tensor-core wait of an acs_mlp_forward / acs_mlp_train_batch launch on the
+ * current device has given up: ACS_ETIMEOUT the first time (that launch's
+ * scores or gradient are incomplete), ACS_OK if none has. After a give-up the
+ * tensor-core path of the process is closed: acs_mlp_forward,
+ * acs_mlp_train_batch, acs_mlp_adam, acs_apply_prior and this call return
+ * ACS_ESTATE. acs_apply_prior runs the same check before using its scores
+ * (ACS_ETIMEOUT, and the context is poisoned). ACS_ECUDA if the stream
+ * reports an error. */
+acs_status acs_mlp_sync(void* stream);
+
+/* Test hook of the bounded waits (no counterpart in the paper; for tests of
+ * the failure path, never needed otherwise): wait_ns sets the bound of one
+ * tensor-core wait (0 restores the default of 200 ms); phantom = 1 makes the
+ * first wait of every tile poll a second mbarrier that nothing arrives on,
+ * so the bound is reached while the tensor core still completes normally.
+ * Process-wide; ACS_EINVAL for a negative bound or a phantom other than 0/1. */
+acs_status acs_mlp_test_wait_hook(int64_t wait_ns, int32_t phantom);
 
 /* One Adam step (Kingma & Ba) on all parameters, step >= 1, in place:
  * m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, p -= lr mhat / (sqrt(vhat)+eps). */

@@ -65,6 +65,10 @@ def load():
     P = ctypes.POINTER
     L.acs_create.argtypes = [_vp, _i32, P(acs_params), P(_vp)]
     L.acs_create_batch.argtypes = [_vp, _vp, _i32, P(acs_params), P(_vp)]
+    L.acs_create_batch_ids.argtypes = [_vp, _vp, _vp, _i32, P(acs_params), P(_vp)]
+    L.acs_state_size.argtypes = [_vp, _i32, _vp]
+    L.acs_get_state.argtypes = [_vp, _i32, _vp, _i64]
+    L.acs_set_state.argtypes = [_vp, _i32, _vp, _i64]
     L.acs_set_stream.argtypes = [_vp, _vp]
     L.acs_run_iterations.argtypes = [_vp, _i32]
     L.acs_best_tour.argtypes = [_vp, _i32, _vp, _vp]
@@ -107,8 +111,13 @@ def load():
     L.acs_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _i32, _f, _f, _f, _f, _vp]
     L.acs_apply_prior.argtypes = [_vp, _i32, _vp, _i32, _vp]
     L.acs_set_candidates.argtypes = [_vp, _i32, _vp, _vp, _i32]
+    L.acs_mlp_sync.argtypes = [_vp]
+    L.acs_mlp_test_wait_hook.argtypes = [_i64, _i32]
     for name in ["acs_prior_features", "acs_prior_count_best_edges", "acs_mlp_forward",
-                 "acs_mlp_train_batch", "acs_mlp_adam", "acs_apply_prior", "acs_set_candidates"]:
+                 "acs_mlp_train_batch", "acs_mlp_adam", "acs_apply_prior", "acs_set_candidates",
+                 "acs_mlp_sync", "acs_mlp_test_wait_hook"]:
+        getattr(L, name).restype = ctypes.c_int
+    for name in ["acs_create_batch_ids", "acs_state_size", "acs_get_state", "acs_set_state"]:
         getattr(L, name).restype = ctypes.c_int
     for name in ["acs_set_threads_per_ant", "acs_autotune", "acs_set_cluster_size", "acs_iterate_noalloc", "acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
                  "acs_best_tour", "acs_get_tours", "acs_get_pheromone", "acs_get_setup",
@@ -151,6 +160,35 @@ def acs_create_batch(coords, offsets, p):
     _check(load().acs_create_batch(_ptr(coords), _ptr(offsets), offsets.shape[0] - 1,
                                    ctypes.byref(p), ctypes.byref(h)), "acs_create_batch")
     return h
+
+
+def acs_create_batch_ids(coords, offsets, instance_ids, p):
+    coords = np.ascontiguousarray(coords, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = None if instance_ids is None else np.ascontiguousarray(instance_ids, np.int32)
+    h = _vp()
+    _check(load().acs_create_batch_ids(_ptr(coords), _ptr(offsets), _ptr(ids),
+                                       offsets.shape[0] - 1, ctypes.byref(p), ctypes.byref(h)),
+           "acs_create_batch_ids")
+    return h
+
+
+def acs_state_size(ctx, instance):
+    b = np.zeros(1, np.int64)
+    _check(load().acs_state_size(ctx, instance, _ptr(b)), "acs_state_size")
+    return int(b[0])
+
+
+def acs_get_state(ctx, instance):
+    """The instance's loop state as an opaque byte image (numpy uint8)."""
+    buf = np.zeros(acs_state_size(ctx, instance), np.uint8)
+    _check(load().acs_get_state(ctx, instance, _ptr(buf), buf.nbytes), "acs_get_state")
+    return buf
+
+
+def acs_set_state(ctx, instance, buf):
+    buf = np.ascontiguousarray(buf, np.uint8)
+    _check(load().acs_set_state(ctx, instance, _ptr(buf), buf.nbytes), "acs_set_state")
 
 
 def acs_set_stream(ctx, stream_handle):
@@ -317,6 +355,10 @@ def acs_mlp_adam(dev_params, dev_grad, dev_m, dev_v, step, lr=1e-3, beta1=0.9, b
                                lr, beta1, beta2, eps, _strm(stream)), "acs_mlp_adam")
 
 
+def acs_mlp_sync(stream=None):
+    _check(load().acs_mlp_sync(_strm(stream)), "acs_mlp_sync")
+
+
 def acs_apply_prior(ctx, instance, dev_p, keep, stream=None):
     _check(load().acs_apply_prior(ctx, instance, _dev(dev_p), keep, _strm(stream)),
            "acs_apply_prior")
@@ -340,14 +382,16 @@ def acs_destroy(ctx):
 class Colony:
     """One context (one instance, or a batch) with numpy in/out."""
 
-    def __init__(self, coords, p, offsets=None):
+    def __init__(self, coords, p, offsets=None, instance_ids=None):
         self.p = p
         coords = np.ascontiguousarray(coords, np.int32)
-        if offsets is None:
+        if offsets is None and instance_ids is None:
             self.ctx = acs_create(coords, p)
             self.sizes = [coords.shape[0]]
         else:
-            self.ctx = acs_create_batch(coords, offsets, p)
+            if offsets is None:
+                offsets = np.array([0, coords.shape[0]], np.int64)
+            self.ctx = acs_create_batch_ids(coords, offsets, instance_ids, p)
             off = np.asarray(offsets, np.int64)
             self.sizes = [int(x) for x in np.diff(off)]
 
@@ -402,6 +446,12 @@ class Colony:
 
     def stats(self, b=0):
         return acs_get_stats(self.ctx, b)
+
+    def get_state(self, b=0):
+        return acs_get_state(self.ctx, b)
+
+    def set_state(self, buf, b=0):
+        acs_set_state(self.ctx, b, buf)
 
     def close(self):
         if self.ctx:

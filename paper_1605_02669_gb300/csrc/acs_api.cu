@@ -231,7 +231,9 @@ struct acs_ctx {
     bool vis_smem = true, xy_smem = false;
     bool spm_resident = true;   // SPM records in shared memory when they fit
     size_t smem = 0;
-    int64_t iteration = 0;
+    int64_t iteration = 0;             // iterations completed by instance 0
+    std::vector<uint8_t> has_best;     // per instance: a best-so-far tour exists
+    std::vector<int32_t> ids;          // per instance: Philox counter word 3
     bool poisoned = false;
     int64_t last_launches = 0;
 };
@@ -444,7 +446,7 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
         D.n = n;
         D.cl = c->cl[b];
         D.W = (n + 31) / 32;
-        D.instance = b;
+        D.instance = c->ids[b];
         D.xy_off = offsets[b];
         D.row_off = offsets[b];
         D.tau_off = (int64_t)tau_total;
@@ -578,7 +580,7 @@ acs_status ctx_view(acs_ctx* c, int b, CtxView* v)
     v->w = c->d_w + 32 * D.row_off;
     v->best = c->d_best + D.node_off;
     v->stream = c->stream;
-    v->has_best = c->iteration > 0;
+    v->has_best = c->has_best[b] != 0;
     return check_device_status(c);
 }
 
@@ -602,8 +604,9 @@ void ctx_poison(acs_ctx* c) { c->poisoned = true; }
 
 extern "C" {
 
-acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets, int32_t B,
-                            const acs_params* p, acs_ctx** out)
+acs_status acs_create_batch_ids(const int32_t* coords, const int64_t* offsets,
+                                const int32_t* instance_ids, int32_t B, const acs_params* p,
+                                acs_ctx** out)
 {
     if (!out) return ACS_EINVAL;
     *out = nullptr;
@@ -620,6 +623,9 @@ acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets, int32
     const int64_t total = offsets[B];
     for (int64_t i = 0; i < 2 * total; ++i)
         if (coords[i] < 0 || coords[i] >= kCoordLimit) return ACS_EINVAL;
+    if (instance_ids)
+        for (int b = 0; b < B; ++b)
+            if (instance_ids[b] < 0) return ACS_EINVAL;
 
     acs_ctx* c = new (std::nothrow) acs_ctx();
     if (!c) return ACS_ENOMEM;
@@ -630,6 +636,9 @@ acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets, int32
     c->max_n = max_n;
     c->n.resize(B);
     c->cl.resize(B);
+    c->has_best.assign(B, 0);
+    c->ids.resize(B);
+    for (int b = 0; b < B; ++b) c->ids[b] = instance_ids ? instance_ids[b] : b;
     for (int b = 0; b < B; ++b) {
         c->n[b] = (int32_t)(offsets[b + 1] - offsets[b]);
         c->cl[b] = std::min(p->cl, c->n[b] - 1);
@@ -644,6 +653,12 @@ acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets, int32
     }
     *out = c;
     return ACS_OK;
+}
+
+acs_status acs_create_batch(const int32_t* coords, const int64_t* offsets, int32_t B,
+                            const acs_params* p, acs_ctx** out)
+{
+    return acs_create_batch_ids(coords, offsets, nullptr, B, p, out);
 }
 
 acs_status acs_create(const int32_t* coords, int32_t n, const acs_params* p, acs_ctx** out)
@@ -692,6 +707,7 @@ acs_status acs_run_iterations(acs_ctx* c, int32_t iters)
         if (e != cudaSuccess) return fail_cuda(c, e);
     }
     c->iteration += iters;
+    std::fill(c->has_best.begin(), c->has_best.end(), (uint8_t)1);
     c->last_launches = (c->p.flags & ACS_FLAG_RELAXED) ? 2ll * iters : iters;
     return ACS_OK;
 }
@@ -790,6 +806,7 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
     }
     if (st == ACS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail_cuda(c, cudaErrorUnknown);
     const int64_t iter0 = c->iteration;
+    const std::vector<uint8_t> has_best0 = c->has_best;
     int best_tpa = c->tpa, best_cs = c->csize;
     bool best_res = c->spm_resident;
     float best_ms = 0.0f;
@@ -829,12 +846,14 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
             if (st == ACS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
                 st = fail_cuda(c, cudaErrorUnknown);
             c->iteration = iter0;
+            c->has_best = has_best0;
         }
     }
     for (Buf& x : bufs) if (x.save) cudaFree(x.save);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     c->iteration = iter0;
+    c->has_best = has_best0;
     c->last_launches = 0;
     c->spm_resident = best_res;
     if (st != ACS_OK) return st;
@@ -885,7 +904,7 @@ acs_status acs_best_tour(acs_ctx* c, int32_t b, int32_t* tour_out, int64_t* len_
     if (c->poisoned) return ACS_ESTATE;
     acs_status s = check_device_status(c);
     if (s != ACS_OK) return s;
-    if (c->iteration == 0) return ACS_ESTATE;
+    if (!c->has_best[b]) return ACS_ESTATE;
     const InstDesc& D = c->desc_h[b];
     cudaError_t e = cudaSuccess;
     if (tour_out) e = cudaMemcpy(tour_out, c->d_best + D.node_off, sizeof(int32_t) * D.n, cudaMemcpyDeviceToHost);
@@ -961,6 +980,195 @@ acs_status acs_get_stats(acs_ctx* c, int32_t b, int64_t out[4])
     cudaError_t e = cudaMemcpy(v, c->d_stats + 4 * (size_t)b, sizeof(v), cudaMemcpyDeviceToHost);
     for (int i = 0; i < 4; ++i) out[i] = (int64_t)v[i];
     return fail_cuda(c, e);
+}
+
+// ---- checkpoint / resume of one instance's loop state (Alg. 1)
+
+namespace {
+
+struct StateHeader {
+    uint32_t magic;       // kStateMagic
+    uint32_t version;     // kStateVersion
+    acs_params p;         // the parameters of the context that wrote it
+    int32_t n, cl;        // nodes, effective candidate width
+    int32_t has_best, pad;
+    int64_t iteration;    // Philox counter word 0 of the next iteration
+    int64_t best_len;     // INT64_MAX when there is no best-so-far tour
+    uint32_t tau0_bits;   // tau0 of the instance (identifies its coordinates)
+    uint32_t pad2;
+    int64_t stats[4];     // fallbacks, selections, SPM hits, SPM misses
+};
+static_assert(sizeof(StateHeader) == 128, "state header layout");
+constexpr uint32_t kStateMagic = 0x53534341u;   // "ACSS"
+constexpr uint32_t kStateVersion = 1;
+
+size_t state_bytes(const acs_ctx* c, int b)
+{
+    const size_t n = (size_t)c->n[b];
+    size_t bytes = sizeof(StateHeader) + 2 * 32 * 4 * n + 4 * n;   // rows, best tour
+    if (c->p.memory == ACS_MEM_MATRIX) bytes += 4 * n * n;
+    else bytes += 8 * n * c->s + 4 * n;
+    return bytes;
+}
+
+bool same_params_but_seed(const acs_params& a, const acs_params& b)
+{
+    return a.m == b.m && a.cl == b.cl && a.beta == b.beta && a.q0 == b.q0 && a.rho == b.rho &&
+           a.xi == b.xi && a.memory == b.memory && a.spm_slots == b.spm_slots &&
+           a.local_period == b.local_period && a.flags == b.flags;
+}
+
+}  // namespace
+
+acs_status acs_state_size(const acs_ctx* c, int32_t b, int64_t* bytes)
+{
+    if (!c || !bytes || b < 0 || b >= c->B) return ACS_EINVAL;
+    *bytes = (int64_t)state_bytes(c, b);
+    return ACS_OK;
+}
+
+acs_status acs_get_state(acs_ctx* c, int32_t b, void* buf, int64_t bytes)
+{
+    if (!c || !buf || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    if (bytes < (int64_t)state_bytes(c, b)) return ACS_EINVAL;
+    acs_status st = check_device_status(c);
+    if (st != ACS_OK) return st;
+    const InstDesc& D = c->desc_h[b];
+    const size_t n = (size_t)D.n;
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kStateMagic;
+    h.version = kStateVersion;
+    h.p = c->p;
+    h.n = D.n;
+    h.cl = D.cl;
+    h.has_best = c->has_best[b];
+    std::memcpy(&h.tau0_bits, &D.tau0, 4);
+    unsigned long long stats[4];
+    cudaError_t e = cudaMemcpy(&h.iteration, c->d_iter + b, 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h.best_len, c->d_best_len + b, 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(stats, c->d_stats + 4 * (size_t)b, sizeof(stats), cudaMemcpyDeviceToHost);
+    for (int i = 0; i < 4; ++i) h.stats[i] = (int64_t)stats[i];
+    size_t o = sizeof(StateHeader);
+    if (e == cudaSuccess) e = cudaMemcpy(out + o, c->d_nn + 32 * D.row_off, 128 * n, cudaMemcpyDeviceToHost);
+    o += 128 * n;
+    if (e == cudaSuccess) e = cudaMemcpy(out + o, c->d_w + 32 * D.row_off, 128 * n, cudaMemcpyDeviceToHost);
+    o += 128 * n;
+    if (e == cudaSuccess) e = cudaMemcpy(out + o, c->d_best + D.node_off, 4 * n, cudaMemcpyDeviceToHost);
+    o += 4 * n;
+    if (c->p.memory == ACS_MEM_MATRIX) {
+        if (e == cudaSuccess) e = cudaMemcpy(out + o, c->d_tau + D.tau_off, 4 * n * n, cudaMemcpyDeviceToHost);
+    } else {
+        const size_t ns = n * c->s;
+        if (e == cudaSuccess) e = cudaMemcpy(out + o, c->d_spm_idx + D.tau_off, 4 * ns, cudaMemcpyDeviceToHost);
+        o += 4 * ns;
+        if (e == cudaSuccess) e = cudaMemcpy(out + o, c->d_tau + D.tau_off, 4 * ns, cudaMemcpyDeviceToHost);
+        o += 4 * ns;
+        if (e == cudaSuccess) e = cudaMemcpy(out + o, c->d_spm_tail + D.node_off, 4 * n, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    std::memcpy(out, &h, sizeof(h));
+    return ACS_OK;
+}
+
+acs_status acs_set_state(acs_ctx* c, int32_t b, const void* buf, int64_t bytes)
+{
+    if (!c || !buf || b < 0 || b >= c->B) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    if (bytes < (int64_t)sizeof(StateHeader)) return ACS_EINVAL;
+    const unsigned char* in = static_cast<const unsigned char*>(buf);
+    StateHeader h;
+    std::memcpy(&h, in, sizeof(h));
+    const InstDesc& D = c->desc_h[b];
+    const int n = D.n;
+    if (h.magic != kStateMagic || h.version != kStateVersion) return ACS_EINVAL;
+    if (h.n != n || !same_params_but_seed(h.p, c->p)) return ACS_EINVAL;
+    if (bytes < (int64_t)state_bytes(c, b)) return ACS_EINVAL;
+    uint32_t tb;
+    std::memcpy(&tb, &D.tau0, 4);
+    if (h.tau0_bits != tb) return ACS_EINVAL;   // other coordinates
+    if (h.cl < 1 || h.cl > std::min(kMaxCl, n - 1) || h.iteration < 0 || h.iteration > INT32_MAX)
+        return ACS_EINVAL;
+    if (h.has_best != 0 && h.has_best != 1) return ACS_EINVAL;
+    // host-side validation of every array before any device write
+    size_t o = sizeof(StateHeader);
+    const int32_t* nn = reinterpret_cast<const int32_t*>(in + o);
+    o += 128 * (size_t)n;
+    const float* w = reinterpret_cast<const float*>(in + o);
+    o += 128 * (size_t)n;
+    const int32_t* best = reinterpret_cast<const int32_t*>(in + o);
+    o += 4 * (size_t)n;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 32; ++k) {
+            int32_t j;
+            float x;
+            std::memcpy(&j, nn + 32 * (size_t)i + k, 4);
+            std::memcpy(&x, w + 32 * (size_t)i + k, 4);
+            if (k < h.cl ? (j < 0 || j >= n || j == i || !(x >= 0.0f)) : j != -1) return ACS_EINVAL;
+        }
+    if (h.has_best) {
+        std::vector<uint8_t> seen((size_t)n, 0);
+        for (int i = 0; i < n; ++i) {
+            int32_t t;
+            std::memcpy(&t, best + i, 4);
+            if (t < 0 || t >= n || seen[t]) return ACS_EINVAL;
+            seen[t] = 1;
+        }
+        if (h.best_len <= 0 || h.best_len == INT64_MAX) return ACS_EINVAL;
+    } else if (h.best_len != INT64_MAX) {
+        return ACS_EINVAL;
+    }
+    if (c->p.memory == ACS_MEM_SPM) {
+        const size_t ns = (size_t)n * c->s;
+        const unsigned char* p = in + o;
+        for (size_t i = 0; i < ns; ++i) {
+            int32_t j;
+            std::memcpy(&j, p + 4 * i, 4);
+            if (j < -1 || j >= n) return ACS_EINVAL;
+        }
+        for (int i = 0; i < n; ++i) {
+            int32_t t;
+            std::memcpy(&t, p + 8 * ns + 4 * (size_t)i, 4);
+            if (t < 0 || t >= c->s) return ACS_EINVAL;
+        }
+    }
+    acs_status st = check_device_status(c);
+    if (st != ACS_OK) return st;
+    cudaStream_t s = c->stream;
+    unsigned long long stats[4];
+    for (int i = 0; i < 4; ++i) stats[i] = (unsigned long long)h.stats[i];
+    o = sizeof(StateHeader);
+    cudaError_t e = cudaMemcpyAsync(c->d_nn + 32 * D.row_off, in + o, 128 * (size_t)n, cudaMemcpyHostToDevice, s);
+    o += 128 * (size_t)n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_w + 32 * D.row_off, in + o, 128 * (size_t)n, cudaMemcpyHostToDevice, s);
+    o += 128 * (size_t)n;
+    if (e == cudaSuccess && h.has_best)
+        e = cudaMemcpyAsync(c->d_best + D.node_off, in + o, 4 * (size_t)n, cudaMemcpyHostToDevice, s);
+    o += 4 * (size_t)n;
+    if (c->p.memory == ACS_MEM_MATRIX) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_tau + D.tau_off, in + o, 4 * (size_t)n * n, cudaMemcpyHostToDevice, s);
+    } else {
+        const size_t ns = (size_t)n * c->s;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_spm_idx + D.tau_off, in + o, 4 * ns, cudaMemcpyHostToDevice, s);
+        o += 4 * ns;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_tau + D.tau_off, in + o, 4 * ns, cudaMemcpyHostToDevice, s);
+        o += 4 * ns;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_spm_tail + D.node_off, in + o, 4 * (size_t)n, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_iter + b, &h.iteration, 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_best_len + b, &h.best_len, 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_stats + 4 * (size_t)b, stats, sizeof(stats), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(c, e);
+    if (h.cl != D.cl) {
+        e = ctx_set_cl(c, b, h.cl);
+        if (e != cudaSuccess) return fail_cuda(c, e);
+    }
+    c->has_best[b] = (uint8_t)h.has_best;
+    if (b == 0) c->iteration = h.iteration;
+    return ACS_OK;
 }
 
 int64_t acs_iteration(const acs_ctx* c) { return c ? c->iteration : -1; }

@@ -73,6 +73,26 @@ constexpr int kTcRows = 128;
 constexpr int kTcMaxGroups = 8;
 constexpr int kK1 = 16, kK2 = 80;   // K of layer 1 (8 features, 3 bias columns) and layer 2 (64 + 3)
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bound of one MMA-completion wait
+// After a wait gave up, the bound of the wait for the MMA that was already
+// issued: tensor memory is freed only once it has signalled completion.
+constexpr unsigned long long kDrainNs = 2000ull * 1000 * 1000;
+
+// Wait bounds handed to the tensor-core kernels. ns: bound of one wait.
+// phantom != 0 (set only through the test hook acs_mlp_test_wait_hook) makes
+// the first wait of every tile poll a second mbarrier that nothing arrives
+// on, so the bound is reached while the real MMA still commits to its own
+// barrier, which the failure path then drains.
+struct TcWait {
+    unsigned long long ns;
+    int phantom;
+};
+
+// Status word of the tensor-core kernels on this device: 0, or ACS_ETIMEOUT
+// once a bounded wait has given up (never cleared: the scores or gradients of
+// that launch are incomplete, and the host refuses later tensor-core work).
+__device__ int32_t g_tc_status;
+// Set by apply_prior_kernel when a score is not a probability.
+__device__ int32_t g_bad_score;
 // instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
 // bits 17-22, M >> 4 in bits 24-28
@@ -90,6 +110,7 @@ struct TcGroup {
     uint16_t x[kTcRows * kK1];    // layer-1 A: 16 row groups x 2 K groups
     uint16_t h1[kTcRows * kK2];   // layer-2 A: 16 row groups x 10 K groups
     unsigned long long bar;       // MMA completion barrier
+    unsigned long long phantom;   // never arrived on (test hook of the bounded wait)
 };
 constexpr size_t kTcWeightBytes = (sizeof(TcWeights) + 127) & ~size_t(127);
 constexpr size_t kTcGroupBytes = (sizeof(TcGroup) + 127) & ~size_t(127);
@@ -182,8 +203,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32])
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // Waits for the completion of phase `parity` of the barrier; gives up after
-// kWaitNs of wall time (%globaltimer) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// `ns` of wall time (%globaltimer) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long ns)
 {
     unsigned long long t0 = 0ull;
     for (;;) {
@@ -198,7 +219,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
         unsigned long long now;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
         if (t0 == 0ull) t0 = now;
-        else if (now - t0 > kWaitNs) return false;
+        else if (now - t0 > ns) return false;
     }
 }
 
@@ -224,7 +245,8 @@ __device__ __forceinline__ uint4 bias_row(float b, bool ones)
 }
 
 __global__ void __launch_bounds__(kTcRows * kTcMaxGroups, 1)
-mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float* pout, uint32_t tmem_cols)
+mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float* pout, uint32_t tmem_cols,
+                      TcWait wt)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
     TcWeights& W = *reinterpret_cast<TcWeights*>(tsm);
@@ -272,8 +294,10 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
     *reinterpret_cast<uint4*>(&G.h1[core_idx(t, 64, kK2 / 8)]) = bias_row(0.0f, true);
     *reinterpret_cast<uint4*>(&G.h1[core_idx(t, 72, kK2 / 8)]) = make_uint4(0u, 0u, 0u, 0u);
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&G.bar);
+    const uint32_t ph = (uint32_t)__cvta_generic_to_shared(&G.phantom);
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ph) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -307,7 +331,7 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
             tc_mma(dcol, da1, db1, kIdescM128N64, 0u);
             tc_commit(bar);
         }
-        ok = mbar_wait(bar, parity);
+        ok = wt.phantom ? mbar_wait(ph, 0u, wt.ns) : mbar_wait(bar, parity, wt.ns);
         if (group_sync_or(bid, !ok)) {
             ok = false;   // every thread of the group takes the failure path
             break;
@@ -342,7 +366,7 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
                 tc_mma(dcol, da2 + 16u * kk, db2 + 16u * kk, kIdescM128N64, kk > 0 ? 1u : 0u);
             tc_commit(bar);
         }
-        ok = mbar_wait(bar, parity);
+        ok = mbar_wait(bar, parity, wt.ns);
         if (group_sync_or(bid, !ok)) {
             ok = false;   // every thread of the group takes the failure path
             break;
@@ -361,18 +385,21 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
         if (row < rows) pout[row] = sigmoidf(z);
         tc_fence_before();
     }
+    bool drained = true;
     if (!ok) {
-        // a wait gave up: allow the MMA in flight one more bounded wait, and
-        // leave NaN in every row of this group that was not scored
-        mbar_wait(bar, parity);
+        // a wait gave up: raise the status, wait (bounded) for the MMA already
+        // issued, and leave NaN in every row of this group that was not scored
+        if (t == 0) atomicExch(&g_tc_status, (int32_t)ACS_ETIMEOUT);
+        drained = mbar_wait(bar, parity, kDrainNs);
         for (; tile < tiles; tile += gstride) {
             const int64_t row = tile * kTcRows + t;
             if (row < rows) pout[row] = __int_as_float(0x7fc00000);
         }
     }
     tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
+    // tensor memory is freed only when no MMA of the CTA can still be in flight
+    const bool can_free = __syncthreads_and(drained);
+    if (warp == 0 && can_free) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols)
                      : "memory");
@@ -418,6 +445,7 @@ struct TrainSmem {
     float b3;
     uint32_t tmem;
     unsigned long long bar;
+    unsigned long long phantom;   // never arrived on (test hook of the bounded wait)
 };
 static_assert(offsetof(TrainSmem, w2) % 128 == 0 && offsetof(TrainSmem, w2n) % 128 == 0 &&
                   offsetof(TrainSmem, x) % 128 == 0 && offsetof(TrainSmem, h1) % 128 == 0 &&
@@ -437,7 +465,7 @@ __device__ __forceinline__ void stage_column_sums(const float* stage, float* red
 
 __global__ void __launch_bounds__(kTcRows, 1)
 mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64_t total, int64_t first,
-                 int64_t batch, int64_t pa, int64_t pc, float* grad, float* loss)
+                 int64_t batch, int64_t pa, int64_t pc, float* grad, float* loss, TcWait wt)
 {
     extern __shared__ __align__(128) unsigned char tsm[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(tsm);
@@ -485,8 +513,10 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
         *reinterpret_cast<uint4*>(&S.at[core_idx(m, k, kKr / 8)]) = make_uint4(0u, 0u, 0u, 0u);
     }
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
+    const uint32_t ph = (uint32_t)__cvta_generic_to_shared(&S.phantom);
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ph) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -533,7 +563,7 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
             tc_mma(tmem, dx, dw1, kIdescM128N64, 0u);
             tc_commit(bar);
         }
-        ok = mbar_wait(bar, parity);
+        ok = wt.phantom ? mbar_wait(ph, 0u, wt.ns) : mbar_wait(bar, parity, wt.ns);
         if (__syncthreads_or(!ok)) {
             ok = false;   // every thread takes the failure path
             break;
@@ -578,7 +608,7 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
                 tc_mma(tmem, dh1a + 16u * kk, dw2 + 16u * kk, kIdescM128N64, kk > 0 ? 1u : 0u);
             tc_commit(bar);
         }
-        ok = mbar_wait(bar, parity);
+        ok = mbar_wait(bar, parity, wt.ns);
         if (__syncthreads_or(!ok)) {
             ok = false;   // every thread takes the failure path
             break;
@@ -636,7 +666,7 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
             tc_commit(bar);
         }
         stage_column_sums(S.stage, S.red + 64, t);
-        ok = mbar_wait(bar, parity);
+        ok = mbar_wait(bar, parity, wt.ns);
         if (__syncthreads_or(!ok)) {
             ok = false;   // every thread takes the failure path
             break;
@@ -676,7 +706,7 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
         }
         any = true;
         stage_column_sums(S.stage, S.red, t);   // db1
-        ok = mbar_wait(bar, parity);
+        ok = mbar_wait(bar, parity, wt.ns);
         if (__syncthreads_or(!ok)) {
             ok = false;   // every thread takes the failure path
             break;
@@ -684,11 +714,15 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
         parity ^= 1u;
         tc_fence_after();
     }
+    bool drained = true;
     if (!ok) {
-        // a wait gave up: one more bounded wait for the MMA in flight; the
-        // loss becomes NaN and no gradient is added
-        mbar_wait(bar, parity);
-        if (t == 0) atomicAdd(loss, __int_as_float(0x7fc00000));
+        // a wait gave up: raise the status, wait (bounded) for the MMA already
+        // issued; the loss becomes NaN and no gradient is added
+        if (t == 0) {
+            atomicExch(&g_tc_status, (int32_t)ACS_ETIMEOUT);
+            atomicAdd(loss, __int_as_float(0x7fc00000));
+        }
+        drained = mbar_wait(bar, parity, kDrainNs);
     } else {
         if (any) {   // Dw rows: 0-63 dW2[in][out] (columns 0-63), 64-71 dW1[f][h] (columns 64-127)
             const int m = warp * 32 + (t & 31);
@@ -729,8 +763,9 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
         }
     }
     tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
+    // tensor memory is freed only when no MMA of the CTA can still be in flight
+    const bool can_free = __syncthreads_and(drained);
+    if (warp == 0 && can_free) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256u) : "memory");
     }
@@ -828,6 +863,7 @@ __global__ void apply_prior_kernel(int32_t* nn, float* w, const float* score, in
     const size_t e = (size_t)i * 32 + lane;
     const bool valid = lane < cl;
     const float p = valid ? score[e] : -1.0f;
+    if (valid && !(p >= 0.0f && p <= 1.0f)) atomicExch(&g_bad_score, 1);
     const int j = nn[e];
     const float wv = w[e];
     int rank = 0;   // candidates that beat this one
@@ -851,6 +887,31 @@ __global__ void apply_prior_kernel(int32_t* nn, float* w, const float* score, in
 }
 
 acs_status launched(cudaError_t e) { return e == cudaSuccess ? ACS_OK : ACS_ECUDA; }
+
+// Host side of the tensor-core status: the bounds the kernels get, and
+// whether a give-up has been reported (then the MLP calls refuse to launch).
+TcWait g_wait = {kWaitNs, 0};
+bool g_tc_failed = false;
+
+// Reads (after synchronising `st`) the device status word; on a recorded
+// give-up marks the tensor-core path failed and returns ACS_ETIMEOUT.
+acs_status tc_status(cudaStream_t st)
+{
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return ACS_ECUDA;
+    }
+    int32_t v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return ACS_ECUDA;
+    }
+    if (v != 0) {
+        g_tc_failed = true;
+        return ACS_ETIMEOUT;
+    }
+    return ACS_OK;
+}
 
 }  // namespace
 
@@ -900,6 +961,7 @@ acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, in
 {
     if (rows == 0) return ACS_OK;
     if (!dev_params || !dev_feat || !dev_p || rows < 0 || ((uintptr_t)dev_feat & 15)) return ACS_EINVAL;
+    if (g_tc_failed) return ACS_ESTATE;
     if (cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tc_smem(kTcMaxGroups)) != cudaSuccess)
         return ACS_ECUDA;
@@ -915,7 +977,7 @@ acs_status acs_mlp_forward(const float* dev_params, const uint16_t* dev_feat, in
     const int64_t ctas = (tiles + groups - 1) / groups;
     const int grid = (int)(ctas < sms ? ctas : sms);
     mlp_forward_tc_kernel<<<grid, kTcRows * groups, tc_smem(groups), (cudaStream_t)stream>>>(
-        dev_params, dev_feat, rows, dev_p, tc_tmem_cols(groups));
+        dev_params, dev_feat, rows, dev_p, tc_tmem_cols(groups), g_wait);
     return launched(cudaGetLastError());
 }
 
@@ -926,6 +988,7 @@ acs_status acs_mlp_train_batch(const float* dev_params, const uint16_t* dev_feat
     if (!dev_params || !dev_feat || !dev_label || !dev_grad || !dev_loss || total < 1 || batch < 1 ||
         first < 0 || perm_a < 1 || perm_c < 0 || ((uintptr_t)dev_feat & 15))
         return ACS_EINVAL;
+    if (g_tc_failed) return ACS_ESTATE;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(dev_grad, 0, sizeof(float) * ACS_MLP_PARAMS, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dev_loss, 0, sizeof(float), st);
@@ -939,7 +1002,7 @@ acs_status acs_mlp_train_batch(const float* dev_params, const uint16_t* dev_feat
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)(blocks < sms ? blocks : sms);
     mlp_train_kernel<<<grid, kTcRows, smem, st>>>(dev_params, dev_feat, dev_label, total, first, batch,
-                                                  perm_a, perm_c, dev_grad, dev_loss);
+                                                  perm_a, perm_c, dev_grad, dev_loss, g_wait);
     return launched(cudaGetLastError());
 }
 
@@ -947,6 +1010,7 @@ acs_status acs_mlp_adam(float* dev_params, const float* dev_grad, float* dev_m, 
                         float lr, float beta1, float beta2, float eps, void* stream)
 {
     if (!dev_params || !dev_grad || !dev_m || !dev_v || step < 1) return ACS_EINVAL;
+    if (g_tc_failed) return ACS_ESTATE;
     // bias corrections in double: 1 - beta2^t cancels heavily in FP32 for small t
     const float c1 = (float)(1.0 - pow((double)beta1, (double)step));
     const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
@@ -961,12 +1025,26 @@ acs_status acs_apply_prior(acs_ctx* ctx, int32_t instance, const float* dev_p, i
     if (!dev_p) return ACS_EINVAL;
     if (acs_status s = ctx_view(ctx, instance, &v)) return s;
     if (keep < 1 || keep > v.cl) return ACS_EINVAL;
+    if (g_tc_failed) return ACS_ESTATE;
     cudaStream_t st = (cudaStream_t)stream;
+    // scores from a scoring launch whose wait gave up are incomplete
+    if (acs_status ts = tc_status(st)) {
+        ctx_poison(ctx);
+        return ts;
+    }
     apply_prior_kernel<<<(v.n + 7) / 8, 256, 0, st>>>(v.nn, v.w, dev_p, v.n, v.cl, keep);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = ctx_set_cl(ctx, instance, keep);
+    int32_t bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&bad, g_bad_score, sizeof(bad));
+    if (e == cudaSuccess && bad) {
+        const int32_t zero = 0;
+        cudaMemcpyToSymbol(g_bad_score, &zero, sizeof(zero));
+        e = cudaErrorInvalidValue;   // rows rewritten from scores that are not probabilities
+    }
     if (e != cudaSuccess) {
+        cudaGetLastError();
         ctx_poison(ctx);
         return ACS_ECUDA;
     }
@@ -1007,6 +1085,20 @@ acs_status acs_set_candidates(acs_ctx* ctx, int32_t instance, const int32_t* nn,
         ctx_poison(ctx);
         return ACS_ECUDA;
     }
+    return ACS_OK;
+}
+
+acs_status acs_mlp_sync(void* stream)
+{
+    if (g_tc_failed) return ACS_ESTATE;
+    return tc_status((cudaStream_t)stream);
+}
+
+acs_status acs_mlp_test_wait_hook(int64_t wait_ns, int32_t phantom)
+{
+    if (wait_ns < 0 || (phantom != 0 && phantom != 1)) return ACS_EINVAL;
+    g_wait.ns = wait_ns == 0 ? kWaitNs : (unsigned long long)wait_ns;
+    g_wait.phantom = phantom;
     return ACS_OK;
 }
 

@@ -151,6 +151,8 @@ class Trainer:
         for first in range(0, total, batch):
             acc += self.batch(feat, label, first, min(batch, total - first), a, c)
             nb += 1
+        # raises if a tensor-core wait of this epoch gave up (incomplete gradients)
+        acs.acs_mlp_sync(_stream())
         return float(acc.item()) / nb
 
 

@@ -188,6 +188,102 @@ def test_train_batch_gradient_matches_fp64(oracle_mod, rows):
     _check_grad(grad.cpu().numpy(), ref_g, float(loss.item()), ref_loss)
 
 
+def test_train_batch_gradient_many_tiles_per_cta(oracle_mod):
+    # the grid is at most one CTA per SM, so beyond 128 x SMs rows every CTA
+    # walks several tiles and accumulates their weight gradients in TMEM (the
+    # accumulate flag after the first tile, operand tiles reused): this size
+    # gives every CTA two or three tiles and a ragged last tile
+    prior = _prior()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rows = 50001
+    assert rows > 2 * 128 * sms
+    x = _edge_rows(instances.clustered(1600, seed=16))[:rows]
+    bits = _bf16_bits(x)
+    y = _labels(rows, 12)
+    P = _params64(18)
+    grad = torch.full((acs.ACS_MLP_PARAMS,), 7.0, device="cuda")
+    loss = torch.full((1,), 7.0, device="cuda")
+    acs.acs_mlp_train_batch(_dev(prior.pack(P)), _dev(bits.view(np.int16)), _dev(y), rows, 0,
+                            rows, 1, 0, grad, loss, torch.cuda.current_stream())
+    ref_loss, ref_g = mlp.backward(P, _bits_to_f64(bits), y.astype(np.float64))
+    _check_grad(grad.cpu().numpy(), ref_g, float(loss.item()), ref_loss)
+
+
+_TIMEOUT_CHILD = r"""
+import json, sys
+sys.path.insert(0, ROOT)
+import numpy as np, torch
+from paper_1605_02669_gb300 import acs, instances
+L = acs.load()
+s = torch.cuda.current_stream()
+params = (torch.randn(acs.ACS_MLP_PARAMS, device="cuda") * 0.2).float()
+rows = 5000
+feat = torch.randn(rows, 8, device="cuda").to(torch.bfloat16).view(torch.int16)
+out = []
+if KIND == "forward":
+    p = torch.empty(rows, device="cuda")
+    acs.acs_mlp_forward(params, feat, rows, p, s)
+    out.append(L.acs_mlp_sync(None))                  # a normal launch: 0
+    ok_scores = bool(torch.isfinite(p).all())
+    col = acs.Colony(instances.uniform(200, seed=1), acs.params(m=8, cl=32))
+    out.append(L.acs_mlp_test_wait_hook(1000000, 1))  # 1 ms, phantom barrier
+    p2 = torch.zeros(rows, device="cuda")
+    acs.acs_mlp_forward(params, feat, rows, p2, s)    # the launch itself succeeds
+    torch.cuda.synchronize()
+    nan_rows = bool(torch.isnan(p2).all())
+    sc = torch.full((200 * 32,), 0.5, device="cuda")
+    out.append(L.acs_apply_prior(col.ctx, 0, acs._dev(sc), 16, None))   # ETIMEOUT, poisons ctx
+    out.append(L.acs_run_iterations(col.ctx, 1))                        # ESTATE
+    out.append(L.acs_mlp_sync(None))                                     # ESTATE
+    out.append(L.acs_mlp_forward(acs._dev(params), acs._dev(feat), rows, acs._dev(p2), None))
+    print("RESULT " + json.dumps({"codes": out, "first_ok": ok_scores, "nan": nan_rows}))
+else:
+    y = torch.zeros(rows, device="cuda")
+    grad = torch.zeros(acs.ACS_MLP_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    out.append(L.acs_mlp_test_wait_hook(1000000, 1))
+    acs.acs_mlp_train_batch(params, feat, y, rows, 0, rows, 1, 0, grad, loss, s)
+    torch.cuda.synchronize()
+    nan_loss = bool(torch.isnan(loss).all())
+    out.append(L.acs_mlp_sync(None))                                     # ETIMEOUT
+    out.append(L.acs_mlp_train_batch(acs._dev(params), acs._dev(feat), acs._dev(y), rows, 0, rows,
+                                     1, 0, acs._dev(grad), acs._dev(loss), None))   # ESTATE
+    out.append(L.acs_mlp_adam(acs._dev(params), acs._dev(grad), acs._dev(grad), acs._dev(grad),
+                              1, 1e-3, 0.9, 0.999, 1e-8, None))                    # ESTATE
+    print("RESULT " + json.dumps({"codes": out, "first_ok": True, "nan": nan_loss}))
+"""
+
+
+@pytest.mark.parametrize("kind", ["forward", "train"])
+def test_tensor_core_wait_give_up_reports_etimeout(kind):
+    # the bounded mbarrier wait of the tcgen05 kernels is driven to its limit by
+    # the test hook (a second barrier that nothing arrives on; the real MMA
+    # still completes and is drained before tensor memory is freed). The give-up
+    # must reach the caller as ACS_ETIMEOUT and close the tensor-core path.
+    # A child process: the closed path would otherwise stay closed for the
+    # tests that follow.
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = "ROOT = %r\nKIND = %r\n" % (root, kind) + _TIMEOUT_CHILD
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    import json
+
+    line = [l for l in r.stdout.splitlines() if l.startswith("RESULT ")][-1]
+    res = json.loads(line[len("RESULT "):])
+    codes, ok_first, nan_out = res["codes"], res["first_ok"], res["nan"]
+    E = acs
+    if kind == "forward":
+        assert codes == [E.ACS_OK, E.ACS_OK, E.ACS_ETIMEOUT, E.ACS_ESTATE, E.ACS_ESTATE, E.ACS_ESTATE]
+        assert ok_first and nan_out
+    else:
+        assert codes == [E.ACS_OK, E.ACS_ETIMEOUT, E.ACS_ESTATE, E.ACS_ESTATE]
+        assert nan_out
+
+
 def test_train_batch_reads_the_affine_permutation(oracle_mod):
     prior = _prior()
     x = _edge_rows(instances.uniform(300, seed=7))     # 9600 rows

@@ -116,3 +116,64 @@ def test_exchange_over_three_gloo_ranks_offers_the_shortest_tour():
             assert offered == []          # the winner keeps its own
         else:
             assert offered == [[0, 1, 2, 3, 4, 5]]
+
+
+def _shard_worker(rank, world, port, out):
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        res = {}
+        for wl in ("batch256", "large16"):
+            bench.select_workload(wl)
+            ids, xy, off, sizes, seed, job_sizes, scaling = bench.rank_share(rank, world)
+            # every rank learns every share over the process group (host only)
+            shares = [None] * world
+            dist.all_gather_object(shares, list(ids))
+            res[wl] = (shares, sizes, job_sizes, scaling, seed, int(off[-1]), xy.shape[0])
+        out[rank] = res
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_batched_workloads_shard_by_instance_over_gloo_ranks(world):
+    import bench
+
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_shard_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for wl in ("batch256", "large16"):
+        bench.select_workload(wl)
+        all_sizes = list(bench.SIZES)
+        work = [bench.M * (n - 1) for n in all_sizes]
+        shares = res[0][wl][0]
+        for r in range(world):
+            assert res[r][wl][0] == shares          # every rank agrees on the split
+            _, sizes, job_sizes, scaling, seed, nodes, rows = res[r][wl]
+            assert scaling == "strong" and job_sizes == all_sizes and seed == 1
+            assert sizes == [all_sizes[b] for b in shares[r]]
+            assert nodes == rows == sum(sizes)
+        flat = sorted(b for sh in shares for b in sh)
+        assert flat == list(range(len(all_sizes)))  # each instance exactly once
+        loads = [sum(work[b] for b in sh) for sh in shares]
+        assert max(loads) - min(loads) <= max(work)  # LPT: within one instance
+
+
+def test_lpt_partition_small_cases():
+    from paper_1605_02669_gb300 import shard
+
+    assert shard.lpt_partition([10, 10, 10], 1, 1) == [[0, 1, 2]]
+    # decreasing work, ties to the lower id and the lower rank
+    # work 8, 16, 16, 4: 1 -> r0, 2 -> r1, 0 -> r0 (tie), 3 -> r1
+    assert shard.lpt_partition([5, 9, 9, 3], 2, 2) == [[0, 1], [2, 3]]
+    assert shard.lpt_partition([4], 1, 3) == [[0], [], []]
+    with pytest.raises(ValueError):
+        shard.lpt_partition([4], 1, 0)
