@@ -294,6 +294,58 @@ def run_reference(args, rank, world):
     }
 
 
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def parallel_oracle_leg(max_seconds=240.0):
+    """The oracle instance-parallel over all host cores (one instance per
+    thread; the ctypes calls release the GIL): one iteration of every instance
+    of the batched workload on the matrix memory, as one CPU job."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    coords = make_coords()
+    cores = os.cpu_count() or 1
+    p = oracle.make_params(m=M, cl=CL, q0=0.9, memory=0, seed=1)
+    t_setup = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        cols = list(ex.map(lambda bx: oracle.Colony(bx[1], p, instance=bx[0]), enumerate(coords)))
+    t_setup = time.perf_counter() - t_setup
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda c: c.run(1), cols))
+    sec = time.perf_counter() - t0
+    units = sum(M * (c.n - 1) for c in cols)
+    for c in cols:
+        c.close()
+    return {"value": units / sec, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "one iteration of all %d instances (matrix), one instance per thread, "
+                      "%.1f s (set-up %.1f s, not timed)" % (len(coords), sec, t_setup)}
+
+
 def cpu_baseline_leg(seconds_budget=15.0):
     """The oracle as it stands, one thread, on a bounded sample of the workload."""
     import oracle
@@ -322,7 +374,8 @@ def cpu_baseline_leg(seconds_budget=15.0):
         c.close()
     return {"value": done_units / t_total, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
             "sample": "%d oracle iterations over %d colonies of the workload (m=%d), "
-                      "single thread, %.1f s" % (ran, len(cols), M, t_total)}
+                      "single thread, %.1f s" % (ran, len(cols), M, t_total),
+            "host": host_cpu()}
 
 
 KERNEL_SOURCES = ["acs_construct.cu", "acs_device.cuh", "acs_internal.cuh"]
@@ -371,38 +424,58 @@ def algorithmic_bytes(n, m, fallbacks, spm):
 
 
 GAP_EVAL = [("clustered", 2392, 301), ("uniform", 5000, 302), ("clustered", 5000, 303)]
+# the learned-prior configuration: 2000 generated training instances, n in
+# [200, 1000], labels from 8 plain-ACS runs of 200 iterations each
+GAP_TRAIN_FULL = {"instances": 2000, "runs": 8, "iters": 200}
+# the benchmark's default, a quarter of the instances with 4 runs of 100
+# iterations (a stated reduction, to keep the default run within minutes)
+GAP_TRAIN_DEFAULT = {"instances": 500, "runs": 4, "iters": 100}
 
 
-def gap_leg(iters, log=None):
+def _replica_batch(coords, reps):
+    """Each held-out instance `reps` times in one batched context: replica r
+    of instance i has instance id i*reps + r, so its own random stream."""
+    xy = np.concatenate([c for c in coords for _ in range(reps)])
+    sizes = [c.shape[0] for c in coords for _ in range(reps)]
+    off = np.zeros(len(sizes) + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    return xy, off, sizes
+
+
+def gap_leg(iters, reps=5, ref_mult=4, train=None, log=None):
     """Tour-length gap at equal GPU time, learned prior vs plain.
 
-    Training: 500 generated instances (n in [200,1000], even b uniform, odd b
-    clustered), labels = best-tour edge frequencies of 4 plain-ACS runs x 100
-    iterations (m=64), 8 epochs of Adam on the library's MLP kernels.
-    Evaluation on held-out instances (n=2392 clustered, n=5000 uniform and
-    clustered), m=128, one batched context each: the plain colony runs `iters`
-    iterations; the prior colony (16 of 32 candidates, w' = w*p) gets the same
-    GPU time. The gap of a run is (L - L*)/L*, L* the best tour either found.
+    Training: generated instances (n in [200,1000], even b uniform, odd b
+    clustered), labels = best-tour edge frequencies of R plain-ACS runs (m=64),
+    8 epochs of Adam on the library's MLP kernels (`train` sets the instances,
+    R and the run length). Evaluation on held-out instances (n=2392 clustered,
+    n=5000 uniform and clustered), m=128: `reps` replicas of each instance in
+    one batched context (own random streams); the plain colony runs `iters`
+    iterations, the prior colony (16 of 32 candidates, w' = w*p) the same GPU
+    time. L* of an instance is the best tour found by any run on it, including
+    an independent reference context (prior-pruned replicas with other
+    instance ids, so other random streams) that runs `ref_mult` times the
+    budget. The gap of a run is
+    (L - L*)/L*; reported as mean and standard deviation over the replicas.
     """
     import torch
 
     from paper_1605_02669_gb300 import acs, instances, prior
 
+    train = dict(GAP_TRAIN_DEFAULT if train is None else train)
     t0 = time.perf_counter()
-    params, losses = prior.train(n_instances=500, n_lo=200, n_hi=1000, runs=4, iters=100, m=64,
-                                 epochs=8, batch=4096, lr=2e-3, seed=11)
+    params, losses = prior.train(n_instances=train["instances"], n_lo=200, n_hi=1000,
+                                 runs=train["runs"], iters=train["iters"], m=64, epochs=8,
+                                 batch=4096, lr=2e-3, seed=11)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    sizes = [n for _, n, _ in GAP_EVAL]
-    xy = np.concatenate([instances.clustered(n, seed=s) if k == "clustered"
-                         else instances.uniform(n, seed=s) for k, n, s in GAP_EVAL])
-    off = np.zeros(len(sizes) + 1, np.int64)
-    off[1:] = np.cumsum(sizes)
-    result = {}
-    budget = None
+    coords = [instances.clustered(n, seed=s) if k == "clustered" else instances.uniform(n, seed=s)
+              for k, n, s in GAP_EVAL]
+    xy, off, sizes = _replica_batch(coords, reps)
     st = torch.cuda.Stream()
-    for mode in ("plain", "prior"):
-        col = acs.Colony(xy, acs.params(m=128, cl=32, seed=7), offsets=off)
+
+    def run(mode, budget_ms=None, n_iters=None, ids=None):
+        col = acs.Colony(xy, acs.params(m=128, cl=32, seed=7), offsets=off, instance_ids=ids)
         if mode == "prior":
             prior.apply(col, params, keep=16)
         col.autotune(trial_iters=1)
@@ -410,35 +483,84 @@ def gap_leg(iters, log=None):
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         gpu_ms, done = 0.0, 0
-        while (budget is None and done < iters) or (budget is not None and gpu_ms < budget):
+        while (budget_ms is None and done < n_iters) or (budget_ms is not None and gpu_ms < budget_ms):
             ev0.record(st)
             col.run(10)
             ev1.record(st)
             ev1.synchronize()
             gpu_ms += ev0.elapsed_time(ev1)
             done += 10
-        if budget is None:
-            budget = gpu_ms
-        result[mode] = {"best": [int(col.best(b)[1]) for b in range(len(sizes))],
-                        "iterations": done, "gpu_ms": gpu_ms}
+        best = [int(col.best(b)[1]) for b in range(len(sizes))]
         col.close()
-    best = [min(a, b) for a, b in zip(result["plain"]["best"], result["prior"]["best"])]
-    for mode in result:
-        result[mode]["gap"] = [(L - Ls) / Ls for L, Ls in zip(result[mode]["best"], best)]
-        result[mode]["mean_gap"] = float(np.mean(result[mode]["gap"]))
-    return {
-        "metric": "mean tour-length gap at equal GPU time (to the best tour either run found)",
-        "plain": result["plain"]["mean_gap"],
-        "prior": result["prior"]["mean_gap"],
-        "unit": "fraction",
-        "higher_is_better": False,
-        "instances": ["%s n=%d" % (k, n) for k, n, _ in GAP_EVAL],
-        "runs": result,
-        "plain_iterations": iters,
-        "m": 128,
-        "train": {"instances": 500, "n": [200, 1000], "label_runs": 4, "label_iters": 100,
-                  "epochs": 8, "final_loss": losses[-1], "seconds": t_train},
-    }
+        return {"best": best, "iterations": done, "gpu_ms": gpu_ms}
+
+    res = {"plain": run("plain", n_iters=iters)}
+    budget = res["plain"]["gpu_ms"]
+    res["prior"] = run("prior", budget_ms=budget)
+    nb = len(sizes)
+    ref_ids = list(range(nb, 2 * nb))
+    res["reference"] = run("prior", budget_ms=ref_mult * budget, ids=ref_ids)
+    out = {"metric": "tour-length gap at equal GPU time to the best tour found on the instance "
+                     "(L*: any run, including an independent reference of %dx the budget)" % ref_mult,
+           "unit": "fraction", "higher_is_better": False, "m": 128, "plain_iterations": iters,
+           "replicas": reps, "instances": {}}
+    for i, (k, n, _) in enumerate(GAP_EVAL):
+        idx = range(i * reps, (i + 1) * reps)
+        Lstar = min(res[mode]["best"][j] for mode in res for j in idx)
+        row = {"L_star": Lstar}
+        for mode in ("plain", "prior"):
+            g = np.array([(res[mode]["best"][j] - Lstar) / Lstar for j in idx])
+            row[mode] = {"mean": float(g.mean()), "std": float(g.std(ddof=1)) if reps > 1 else 0.0,
+                         "best": int(min(res[mode]["best"][j] for j in idx))}
+        out["instances"]["%s n=%d" % (k, n)] = row
+    for mode in ("plain", "prior"):
+        g = np.array([out["instances"][k][mode]["mean"] for k in out["instances"]])
+        out[mode] = float(g.mean())
+    out["iterations"] = {m_: res[m_]["iterations"] for m_ in res}
+    out["gpu_ms"] = {m_: res[m_]["gpu_ms"] for m_ in res}
+    out["train"] = dict(train, n=[200, 1000], epochs=8, final_loss=losses[-1], seconds=t_train,
+                        full_size=train == GAP_TRAIN_FULL)
+    return out
+
+
+def large_prior_leg(iters=20, reps=1):
+    """The large-scale configuration with the learned prior on and off: a
+    prior trained at the default size scores the candidate lists of the 16
+    instances (8 x n=10000, 8 x n=20000, m=256), and both colonies (matrix)
+    run `iters` iterations; reports ant-steps/s and the best tour lengths."""
+    import torch
+
+    from paper_1605_02669_gb300 import acs, prior
+
+    tr = GAP_TRAIN_DEFAULT
+    params, _ = prior.train(n_instances=tr["instances"], n_lo=200, n_hi=1000, runs=tr["runs"],
+                            iters=tr["iters"], m=64, epochs=8, batch=4096, lr=2e-3, seed=11)
+    coords = make_coords()
+    xy = np.concatenate(coords).astype(np.int32)
+    off = np.zeros(len(coords) + 1, np.int64)
+    off[1:] = np.cumsum([c.shape[0] for c in coords])
+    st = torch.cuda.Stream()
+    out = {}
+    for mode in ("plain", "prior"):
+        col = acs.Colony(xy, acs.params(m=M, cl=CL, seed=1), offsets=off)
+        if mode == "prior":
+            prior.apply(col, params, keep=16)
+        col.set_stream(st.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        col.run(iters)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[mode] = {"ant_steps_per_s": sum(M * (n - 1) for n in SIZES) * iters / (ms / 1000.0),
+                     "ms_per_iteration": ms / iters,
+                     "best": [int(col.best(b)[1]) for b in range(len(coords))]}
+        col.close()
+    out["iterations"] = iters
+    out["mean_best_ratio_prior_to_plain"] = float(np.mean(
+        [a / b for a, b in zip(out["prior"]["best"], out["plain"]["best"])]))
+    return out
 
 
 SCORING_ROWS = 1 << 24   # 16.8 M candidate edges (n = 524,288 nodes x 32): 335 MB in and out, > L2
@@ -515,6 +637,111 @@ def relaxed_leg(xy, off, sizes, steps, warmup):
             "ms_per_iteration": total / steps, "memory": "matrix", "best_len": best,
             "note": "relaxed construction (ACS-GPU-Alt): racy local updates, not bit-exact; "
                     "the synchronous deterministic kernels give the main value"}
+
+
+def _time_iterations(cols, steps, warmup, flush=None):
+    """CUDA-event time of `steps` iterations of every colony (each on its own
+    stream, L2 flushed between iterations when `flush` is given)."""
+    import torch
+
+    for _ in range(warmup):
+        for c, _ in cols:
+            c.run(1)
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        torch.cuda.synchronize()
+        evs = []
+        for c, st in cols:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            c.run(1)
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        total += max(e0.elapsed_time(e1) for e0, e1 in evs)
+    return total
+
+
+def late_window_leg(ctxs, sizes, flush, iters, steps=10):
+    """Steady state: the benchmark's colonies continue for `iters` untimed
+    iterations (the pheromone concentrates, the full-scan rate and the SPM hit
+    pattern change), then `steps` iterations are timed like the main value."""
+    import torch
+
+    for _ in range(iters):
+        for c, _ in ctxs:
+            c.run(1)
+    torch.cuda.synchronize()
+    fb0 = [[c.stats(b)[0] for b in range(len(sizes))] for c, _ in ctxs]
+    ms = _time_iterations(ctxs, steps, 0, flush)
+    fb1 = [[c.stats(b)[0] for b in range(len(sizes))] for c, _ in ctxs]
+    units = len(ctxs) * sum(M * (n - 1) for n in sizes) * steps
+    fb = sum(b - a for x, y in zip(fb0, fb1) for a, b in zip(x, y))
+    return {"value": units / (ms / 1000.0), "unit": "ant-steps/s",
+            "iterations_before": int(ctxs[0][0].iteration) - steps, "timed_iterations": steps,
+            "ms_per_step": ms / steps,
+            "fallback_rate": fb / float(len(ctxs) * steps * sum(M * (n - 1) for n in sizes))}
+
+
+def period_sweep_leg(xy, off, sizes, tuning, steps=5, warmup=3):
+    """Ant-steps/s for local-update periods k = 1, 2, 4, 8, 16 (Sec. 4, the
+    paper's updates limited to every k-th step) on the benchmark's instances,
+    both memories, the launch shape the autotuner chose for k = 1."""
+    import torch
+
+    from paper_1605_02669_gb300 import acs
+
+    out = []
+    for k in (1, 2, 4, 8, 16):
+        row = {"k": k}
+        for mem in WORKLOADS[WORKLOAD]["memories"]:
+            st = torch.cuda.Stream()
+            col = acs.Colony(xy, acs.params(m=M, cl=CL, memory=mem, spm_slots=8, local_period=k,
+                                            seed=1), offsets=off)
+            t = tuning[MEM_NAMES[mem]]
+            col.set_cluster_size(t["cluster_size"])
+            col.set_threads_per_ant(t["threads_per_ant"])
+            col.set_stream(st.cuda_stream)
+            ms = _time_iterations([(col, st)], steps, warmup)
+            row[MEM_NAMES[mem]] = sum(M * (n - 1) for n in sizes) * steps / (ms / 1000.0)
+            col.close()
+        out.append(row)
+    return {"unit": "ant-steps/s", "iterations_timed": steps, "rows": out}
+
+
+def slot_sweep_leg(xy, off, sizes, iters=50):
+    """SPM hit ratio (Sec. 3.2, Fig. spm-hit-ratio: hits / (hits + misses) of
+    every record update, local and global) and ant-steps/s against the slots
+    per record s, over the first `iters` iterations on the benchmark's
+    instances."""
+    import torch
+
+    from paper_1605_02669_gb300 import acs
+
+    out = []
+    for s in (1, 2, 4, 8, 16, 32):
+        st = torch.cuda.Stream()
+        col = acs.Colony(xy, acs.params(m=M, cl=CL, memory=acs.ACS_MEM_SPM, spm_slots=s, seed=1),
+                         offsets=off)
+        col.set_stream(st.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        col.run(iters)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = [col.stats(b) for b in range(len(sizes))]
+        row = {"s": s, "ant_steps_per_s": sum(M * (n - 1) for n in sizes) * iters / (ms / 1000.0)}
+        for n, (fb, sel, hit, miss) in zip(sizes, stats):
+            row["hit_ratio_n%d" % n] = hit / float(hit + miss)
+        out.append(row)
+        col.close()
+    return {"iterations": iters, "rows": out,
+            "note": "default launch shape; counts every record update of the run"}
 
 
 def run_ours(args, rank, world, local):
@@ -661,12 +888,28 @@ def run_ours(args, rank, world, local):
                            "nearest-neighbour tour, pheromone init) and a best-tour read "
                            "after every iteration"}
 
+    late = None
+    if rank == 0 and not args.no_late and ctxs:
+        li = args.late_iters if args.late_iters is not None else \
+            {"batch256": 100, "large16": 20}.get(WORKLOAD, 500)
+        late = late_window_leg(ctxs, sizes, flush, li)
     if rank != 0:
         return None
-    gap = None if (args.no_gap or WORKLOAD != "paper") else gap_leg(args.gap_iters)
+    sweeps = None
+    if WORKLOAD == "paper" and not args.no_sweeps:
+        sweeps = {"local_period": period_sweep_leg(xy, off, sizes, tuning),
+                  "spm_slots": slot_sweep_leg(xy, off, sizes)}
+    gap = None if (args.no_gap or WORKLOAD != "paper") else gap_leg(
+        args.gap_iters, reps=args.gap_reps,
+        train=GAP_TRAIN_FULL if args.gap_full_training else GAP_TRAIN_DEFAULT)
+    large_prior = None
+    if WORKLOAD == "large16" and not args.no_gap:
+        large_prior = large_prior_leg()
     relaxed = None if args.no_relaxed else relaxed_leg(xy, off, sizes, args.steps, args.warmup)
     scoring = None if args.no_prior_scoring else prior_scoring_leg(args.steps, args.warmup)
     cpu = None if args.no_cpu_baseline else cpu_baseline_leg()
+    if cpu is not None and WORKLOAD in SHARDED and not args.no_parallel_oracle:
+        cpu["all_cores"] = parallel_oracle_leg()
     return {
         "metric": "ant-steps/s in tour construction",
         "value": value,
@@ -691,7 +934,10 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "gpu_launches": int(launches),
         "tuning": tuning,
+        "late_window": late,
+        "sweeps": sweeps,
         "gap_at_equal_time": gap,
+        "large_prior": large_prior,
         "relaxed": relaxed,
         "prior_scoring": scoring,
     }
@@ -715,10 +961,23 @@ def main():
                     help="skip the relaxed-construction leg")
     ap.add_argument("--gap-iters", type=int, default=1000,
                     help="iterations of the plain colony in the gap leg")
+    ap.add_argument("--gap-reps", type=int, default=5,
+                    help="replicas (own random streams) of each held-out instance in the gap leg")
+    ap.add_argument("--gap-full-training", action="store_true",
+                    help="train the prior at the full configuration (2000 instances, 8 runs x "
+                         "200 iterations) instead of the default quarter size")
     ap.add_argument("--no-prior-scoring", action="store_true",
                     help="skip the learned prior's scoring leg")
     ap.add_argument("--prior-scoring-only", action="store_true",
                     help="run only the learned prior's scoring leg (profiling)")
+    ap.add_argument("--no-late", action="store_true", help="skip the late-window leg")
+    ap.add_argument("--late-iters", type=int, default=None,
+                    help="untimed iterations before the late timed window (default: 500, "
+                         "batch256 100, large16 20)")
+    ap.add_argument("--no-sweeps", action="store_true",
+                    help="skip the local-period and SPM-slot sweeps")
+    ap.add_argument("--no-parallel-oracle", action="store_true",
+                    help="skip the all-cores oracle timing of the batched workloads")
     ap.add_argument("--tpa", type=int, default=0, help="pin lanes per ant instead of autotuning")
     ap.add_argument("--cluster", type=int, default=0, help="pin the cluster size instead of autotuning")
     args = ap.parse_args()
