@@ -53,24 +53,40 @@ def _assert_same(gpu, ref, memory, b):
         assert np.array_equal(gv.view(np.uint32), rv.view(np.uint32))
 
 
-def test_batched_256_instances(oracle_mod):
+@pytest.mark.parametrize("memory", [0, 1])
+def test_batched_256_instances(oracle_mod, memory):
     # 256 instances, n uniform in [100, 2500], even b uniform / odd b clustered,
-    # m=64, 32-NN, one launch per iteration for the whole batch
+    # m=64, 32-NN, one launch per iteration for the whole batch; on the SPM
+    # with the records in global memory, the placement the autotuner picks
+    # for this batch
     xy, off, sizes, kinds = instances.mixed_batch(256, 100, 2500, seed=3)
-    p = acs.params(m=64, cl=32, q0=0.9, seed=7)
+    p = acs.params(m=64, cl=32, q0=0.9, memory=memory, spm_slots=8, seed=7)
     gpu = acs.Colony(xy, p, offsets=off)
+    if memory == 1:
+        gpu.set_spm_resident(0)
     gpu.run(2)
     for b in range(256):
         t, L = gpu.tours(b)
         bt, bl = gpu.best(b)
         _check_properties(xy[off[b]:off[b + 1]], t, L, bt, bl)
-    # bit-exact against the oracle on the smallest, a middle and the largest instance
+    # bit-exact against the oracle on 32 instances: the smallest, the largest
+    # and 30 spread over the size order (the oracle colonies run in threads)
+    from concurrent.futures import ThreadPoolExecutor
+
     order = np.argsort(sizes)
-    for b in (int(order[0]), int(order[128]), int(order[-1])):
-        ref = oracle.Colony(xy[off[b]:off[b + 1]], oracle.make_params(m=64, cl=32, q0=0.9, seed=7),
-                            instance=b)
-        ref.run(2)
-        _assert_same(gpu, ref, 0, b)
+    pick = sorted({int(order[i]) for i in np.linspace(0, 255, 32).round().astype(int)})
+
+    def ref_of(b):
+        r = oracle.Colony(xy[off[b]:off[b + 1]],
+                          oracle.make_params(m=64, cl=32, q0=0.9, memory=memory, spm_slots=8, seed=7),
+                          instance=b)
+        r.run(2)
+        return r
+
+    with ThreadPoolExecutor(16) as ex:
+        refs = list(ex.map(ref_of, pick))
+    for b, ref in zip(pick, refs):
+        _assert_same(gpu, ref, memory, b)
 
 
 @pytest.mark.parametrize("memory", [0, 1])
