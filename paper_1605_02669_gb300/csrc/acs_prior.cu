@@ -134,12 +134,14 @@ __device__ __forceinline__ int core_idx(int r, int k, int kg)
 }
 
 // shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
-// byte offset >> 4 (bits 16-29) = 128 B, stride byte offset >> 4 (bits 32-45),
-// descriptor version 1 (bits 46-48), base offset 0, no swizzle (bits 61-63 = 0)
-__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t sbo)
+// byte offset >> 4 (bits 16-29; the distance between K-adjacent core
+// matrices, 128 B when they are packed), stride byte offset >> 4 (bits 32-45;
+// between 8-row groups), descriptor version 1 (bits 46-48), base offset 0,
+// no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t sbo, uint32_t lbo = 128u)
 {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
@@ -421,11 +423,24 @@ mlp_forward_tc_kernel(const float* P, const uint16_t* feat, int64_t rows, float*
 // h1^T, rows 64-71 x^T, the rest zero; columns 0-63 of B are dh2, 64-127
 // dh1 (both BF16), so the two diagonal blocks of Dw are dW2 and dW1 and the
 // off-diagonal ones are not used. Transposed operands are written by the
-// epilogues element by element. The bias and w3 gradients are FP32 column
+// epilogues element by element, into tiles whose core matrices are padded
+// along K to 144 B (leading byte offset 144 instead of 128): a warp then
+// writes 32 K-consecutive values of one row into four 16-byte pieces on
+// distinct banks instead of four pieces on the same four banks. The bias and w3 gradients are FP32 column
 // sums over the tile, staged through shared memory. Dw sits in TMEM columns
 // 128-255 and is added into the gradient once per CTA.
 
 constexpr int kKr = kTcRows;   // K of the weight-gradient GEMM: the tile's rows
+constexpr int kPadCore = 72;   // elements between K-adjacent core matrices of at / bt (144 B)
+constexpr int kPadRows = kPadCore * (kKr / 8);   // elements between 8-row groups of at / bt
+// descriptor start advance of one K = 16 step (two padded core matrices), in 16-byte units
+constexpr uint32_t kPadStep = 2u * (2u * kPadCore) / 16u;
+
+// element index of (row r, column k) in the padded at / bt tiles
+__device__ __forceinline__ int pad_idx(int r, int k)
+{
+    return (r >> 3) * kPadRows + (k >> 3) * kPadCore + ((r & 7) << 3) + (k & 7);
+}
 constexpr int kStage = 68;     // FP32 staging row (64 + 4: conflict-free 16-byte stores)
 constexpr uint32_t kIdescM128N128 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
@@ -437,8 +452,8 @@ struct TrainSmem {
     uint16_t x[kTcRows * kK1];    // layer-1 A (16 row groups x 2 K groups; K 8-10 constant ones)
     uint16_t h1[kTcRows * kK2];   // layer-2 A (16 x 10; K 64-66 constant ones)
     uint16_t dh2[kTcRows * 64];   // dh1 A: dh2 [row][out]
-    uint16_t at[128 * kKr];       // weight-gradient A: [h1^T ; x^T ; 0] (16 x 16 K groups)
-    uint16_t bt[128 * kKr];       // weight-gradient B: [dh2 | dh1]^T
+    uint16_t at[16 * kPadRows];   // weight-gradient A: [h1^T ; x^T ; 0] (16 x 16 K groups, padded)
+    uint16_t bt[16 * kPadRows];   // weight-gradient B: [dh2 | dh1]^T (padded)
     float stage[kTcRows * kStage];   // FP32 rows for the column sums
     float w3[64];
     float red[3 * 64 + 2];        // b1, b2, w3 gradient sums, b3 sum, loss sum
@@ -510,7 +525,7 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
     *reinterpret_cast<uint4*>(&S.h1[core_idx(t, 72, kK2 / 8)]) = make_uint4(0u, 0u, 0u, 0u);
     for (int i = t; i < 56 * kKr / 8; i += kTcRows) {   // rows 72..127, 16 B at a time
         const int m = 72 + i / (kKr / 8), k = (i % (kKr / 8)) * 8;
-        *reinterpret_cast<uint4*>(&S.at[core_idx(m, k, kKr / 8)]) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(&S.at[pad_idx(m, k)]) = make_uint4(0u, 0u, 0u, 0u);
     }
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
     const uint32_t ph = (uint32_t)__cvta_generic_to_shared(&S.phantom);
@@ -535,7 +550,8 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
     const uint64_t dx = smem_desc(S.x, (kK1 / 8) * 128), dw1 = smem_desc(S.w1, (kK1 / 8) * 128);
     const uint64_t dh1a = smem_desc(S.h1, (kK2 / 8) * 128), dw2 = smem_desc(S.w2, (kK2 / 8) * 128);
     const uint64_t ddh2 = smem_desc(S.dh2, 8 * 128), dw2n = smem_desc(S.w2n, 8 * 128);
-    const uint64_t dat = smem_desc(S.at, (kKr / 8) * 128), dbt = smem_desc(S.bt, (kKr / 8) * 128);
+    const uint64_t dat = smem_desc(S.at, 2 * kPadRows, 2 * kPadCore);
+    const uint64_t dbt = smem_desc(S.bt, 2 * kPadRows, 2 * kPadCore);
     const float inv_b = 1.0f / (float)batch;
     uint32_t parity = 0;
     bool ok = true, any = false;
@@ -552,7 +568,7 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
         {   // x^T into rows 64-71 of the weight-gradient A
             const uint16_t* xs = reinterpret_cast<const uint16_t*>(&xv);
 #pragma unroll
-            for (int f = 0; f < 8; ++f) S.at[core_idx(64 + f, t, kKr / 8)] = xs[f];
+            for (int f = 0; f < 8; ++f) S.at[pad_idx(64 + f, t)] = xs[f];
         }
         // ---- layer 1
         fence_async_smem();
@@ -589,8 +605,8 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {   // h1^T into rows 0-63 of the weight-gradient A
                     const int in = half * 32 + c * 8 + 2 * j;
-                    S.at[core_idx(in, t, kKr / 8)] = (uint16_t)(q[j] & 0xFFFFu);
-                    S.at[core_idx(in + 1, t, kKr / 8)] = (uint16_t)(q[j] >> 16);
+                    S.at[pad_idx(in, t)] = (uint16_t)(q[j] & 0xFFFFu);
+                    S.at[pad_idx(in + 1, t)] = (uint16_t)(q[j] >> 16);
                 }
             }
 #pragma unroll
@@ -650,8 +666,8 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int out = c * 8 + 2 * j;
-                S.bt[core_idx(out, t, kKr / 8)] = (uint16_t)(q[j] & 0xFFFFu);
-                S.bt[core_idx(out + 1, t, kKr / 8)] = (uint16_t)(q[j] >> 16);
+                S.bt[pad_idx(out, t)] = (uint16_t)(q[j] & 0xFFFFu);
+                S.bt[pad_idx(out + 1, t)] = (uint16_t)(q[j] >> 16);
             }
         }
         fence_async_smem();
@@ -689,8 +705,8 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
             for (int j = 0; j < 16; ++j) {   // dh1 as columns 64-127 of the weight-gradient B
                 const uint32_t q = pack_bf16(v[2 * j], v[2 * j + 1]);
                 const int in = half * 32 + 2 * j;
-                S.bt[core_idx(64 + in, t, kKr / 8)] = (uint16_t)(q & 0xFFFFu);
-                S.bt[core_idx(64 + in + 1, t, kKr / 8)] = (uint16_t)(q >> 16);
+                S.bt[pad_idx(64 + in, t)] = (uint16_t)(q & 0xFFFFu);
+                S.bt[pad_idx(64 + in + 1, t)] = (uint16_t)(q >> 16);
             }
         }
         fence_async_smem();
@@ -701,7 +717,7 @@ mlp_train_kernel(const float* P, const uint16_t* feat, const float* label, int64
             tc_fence_after();
 #pragma unroll
             for (int kk = 0; kk < kKr / 16; ++kk)
-                tc_mma(dw, dat + 16u * kk, dbt + 16u * kk, kIdescM128N128, (any || kk > 0) ? 1u : 0u);
+                tc_mma(dw, dat + kPadStep * kk, dbt + kPadStep * kk, kIdescM128N128, (any || kk > 0) ? 1u : 0u);
             tc_commit(bar);
         }
         any = true;
