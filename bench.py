@@ -867,8 +867,16 @@ def run_ours(args, rank, world, local):
         t0 = time.perf_counter()
         cols = []
         for mem in WORKLOADS[WORKLOAD]["memories"]:
-            p = acs.params(m=M, cl=CL, memory=mem, spm_slots=8, seed=1)
-            cols.append(acs.Colony(xy, p, offsets=off, instance_ids=ids))
+            p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
+                           seed=seed)
+            c = acs.Colony(xy, p, offsets=off, instance_ids=ids)
+            # the launch shape the device leg ran with, set through the public
+            # API (a caller that tuned once reuses the shape)
+            t = tuning.get(MEM_NAMES[mem])
+            if t:
+                c.set_cluster_size(t["cluster_size"])
+                c.set_threads_per_ant(t["threads_per_ant"])
+            cols.append(c)
         d2h = 0
         for _ in range(args.steps):
             for c in cols:
@@ -885,7 +893,8 @@ def run_ours(args, rank, world, local):
                "h2d_bytes_per_step": int(2 * xy.nbytes / args.steps + 2 * off.nbytes / args.steps),
                "d2h_bytes_per_step": int(d2h / args.steps),
                "includes": "context creation from host coordinates (candidate lists, "
-                           "nearest-neighbour tour, pheromone init) and a best-tour read "
+                           "nearest-neighbour tour, pheromone init), the device leg's "
+                           "launch shape set through the API, and a best-tour read "
                            "after every iteration"}
 
     late = None
