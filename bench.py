@@ -704,6 +704,8 @@ def period_sweep_leg(xy, off, sizes, tuning, steps=5, warmup=3):
             t = tuning[MEM_NAMES[mem]]
             col.set_cluster_size(t["cluster_size"])
             col.set_threads_per_ant(t["threads_per_ant"])
+            if mem == acs.ACS_MEM_SPM:
+                col.set_spm_resident(1 if t["kernel_mode"] == 2 else 0)
             col.set_stream(st.cuda_stream)
             ms = _time_iterations([(col, st)], steps, warmup)
             row[MEM_NAMES[mem]] = sum(M * (n - 1) for n in sizes) * steps / (ms / 1000.0)
@@ -760,6 +762,10 @@ def run_ours(args, rank, world, local):
     tuning = {}
     mems = {"both": WORKLOADS[WORKLOAD]["memories"], "matrix": (acs.ACS_MEM_MATRIX,),
             "spm": (acs.ACS_MEM_SPM,)}[args.only]
+    # joint tuning of the concurrent colonies, except on large16, where one
+    # trial iteration takes about a second and the joint passes would add
+    # minutes of set-up
+    group_tune = len(mems) > 1 and WORKLOAD != "large16"
     for mem, st in zip(mems if sizes else (), (sA, sB)):
         p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
                        seed=seed)
@@ -770,14 +776,23 @@ def run_ours(args, rank, world, local):
                 col.set_cluster_size(args.cluster)
             if args.tpa:
                 col.set_threads_per_ant(args.tpa)
-        else:
+            if args.spm_resident >= 0 and mem == acs.ACS_MEM_SPM:
+                col.set_spm_resident(args.spm_resident)
+        elif not group_tune:
             # the autotuner picks lanes per ant and cluster size; the state is
             # restored afterwards, so the timed iterations are unaffected
             col.autotune(trial_iters=2)
+        ctxs.append((col, st))
+    if group_tune and ctxs and not (args.tpa or args.cluster):
+        # the colonies run concurrently and compete for the SMs: their shapes
+        # are tuned together (each alone first, then jointly)
+        acs.autotune_group([c for c, _ in ctxs], trial_iters=2)
+    for (col, _), mem in zip(ctxs, mems):
         tuning[MEM_NAMES[mem]] = {"threads_per_ant": col.threads_per_ant,
                                   "cluster_size": col.cluster_size,
                                   "kernel_mode": col.kernel_mode}
-        ctxs.append((col, st))
+    if ctxs:
+        tuning["joint"] = bool(group_tune and len(ctxs) > 1 and not (args.tpa or args.cluster))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(record=None):
@@ -876,6 +891,8 @@ def run_ours(args, rank, world, local):
             if t:
                 c.set_cluster_size(t["cluster_size"])
                 c.set_threads_per_ant(t["threads_per_ant"])
+                if mem == acs.ACS_MEM_SPM:
+                    c.set_spm_resident(1 if t["kernel_mode"] == 2 else 0)
             cols.append(c)
         d2h = 0
         for _ in range(args.steps):
@@ -989,6 +1006,9 @@ def main():
                     help="skip the all-cores oracle timing of the batched workloads")
     ap.add_argument("--tpa", type=int, default=0, help="pin lanes per ant instead of autotuning")
     ap.add_argument("--cluster", type=int, default=0, help="pin the cluster size instead of autotuning")
+    ap.add_argument("--spm-resident", type=int, choices=[-1, 0, 1], default=-1,
+                    help="with --tpa/--cluster: pin the SPM records to global memory (0) or to the "
+                         "cluster's shared memory (1); -1 leaves the choice to the launch planner")
     args = ap.parse_args()
     select_workload(args.workload)
     rank, world, local = dist_setup(args)

@@ -167,6 +167,22 @@ int32_t acs_kernel_mode(const acs_ctx* ctx);
 acs_status acs_autotune(acs_ctx* ctx, int32_t trial_iters, int32_t* chosen_tpa,
                         int32_t* chosen_csize);
 
+/* Joint autotuner (no counterpart in the paper) for k contexts that run
+ * concurrently, each on its own stream (acs_set_stream), for instance one
+ * per pheromone memory. A shape that is fastest alone can be slower beside
+ * the others, which compete for the same SMs. Each context is first tuned
+ * alone (acs_autotune). Then, by coordinate descent over the contexts (two
+ * passes at most), every launch shape of one context is timed with all k
+ * running together, the others' shapes fixed. The shape kept is the one that
+ * gives the shortest group time: from a common start to the end of the
+ * slowest context's `trial_iters` iterations, after one warm-up iteration
+ * each. Every context's state is restored after every trial, so results and
+ * iteration counts are unchanged. ctxs: host array of k distinct contexts.
+ * ACS_EINVAL for a NULL or repeated context, k < 1 or trial_iters < 1;
+ * ACS_ESTATE if one is poisoned; ACS_ENOMEM if a snapshot cannot be
+ * allocated. Synchronous. */
+acs_status acs_autotune_group(acs_ctx* const* ctxs, int32_t k, int32_t trial_iters);
+
 /* Multi-colony exchange (the paper's related work, Sec. 2; no counterpart in
  * its algorithms): offer `tour` (host int32 [n], a permutation of the
  * instance's nodes) as the best-so-far of `instance`. Its length is computed

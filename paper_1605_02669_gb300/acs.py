@@ -94,6 +94,7 @@ def load():
     L.acs_threads_per_ant.argtypes = [_vp]
     L.acs_threads_per_ant.restype = _i32
     L.acs_autotune.argtypes = [_vp, _i32, _vp, _vp]
+    L.acs_autotune_group.argtypes = [_vp, _i32, _i32]
     L.acs_set_cluster_size.argtypes = [_vp, _i32]
     L.acs_cluster_size.argtypes = [_vp]
     L.acs_cluster_size.restype = _i32
@@ -117,7 +118,8 @@ def load():
                  "acs_mlp_train_batch", "acs_mlp_adam", "acs_apply_prior", "acs_set_candidates",
                  "acs_mlp_sync", "acs_mlp_test_wait_hook"]:
         getattr(L, name).restype = ctypes.c_int
-    for name in ["acs_create_batch_ids", "acs_state_size", "acs_get_state", "acs_set_state"]:
+    for name in ["acs_create_batch_ids", "acs_state_size", "acs_get_state", "acs_set_state",
+                 "acs_autotune_group"]:
         getattr(L, name).restype = ctypes.c_int
     for name in ["acs_set_threads_per_ant", "acs_autotune", "acs_set_cluster_size", "acs_iterate_noalloc", "acs_create", "acs_create_batch", "acs_set_stream", "acs_run_iterations",
                  "acs_best_tour", "acs_get_tours", "acs_get_pheromone", "acs_get_setup",
@@ -298,6 +300,17 @@ def acs_autotune(ctx, trial_iters):
     cs = np.zeros(1, np.int32)
     _check(load().acs_autotune(ctx, int(trial_iters), _ptr(tpa), _ptr(cs)), "acs_autotune")
     return int(tpa[0]), int(cs[0])
+
+
+def acs_autotune_group(ctxs, trial_iters):
+    arr = (_vp * len(ctxs))(*ctxs)
+    _check(load().acs_autotune_group(arr, len(ctxs), int(trial_iters)), "acs_autotune_group")
+
+
+def autotune_group(colonies, trial_iters=2):
+    """Tune the launch shapes of colonies that run concurrently on their own
+    streams (acs_autotune_group)."""
+    acs_autotune_group([c.ctx for c in colonies], trial_iters)
 
 
 def acs_iterate_noalloc(dev_coords, n, dev_nn32, dev_w32, cl, tau0, dev_tau, dev_tours,

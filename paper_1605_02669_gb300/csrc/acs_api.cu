@@ -219,6 +219,7 @@ struct acs_ctx {
     uint32_t* d_vis = nullptr;
     float* d_P = nullptr;
     int32_t* d_status = nullptr;
+    int32_t* d_sched = nullptr;   // next-instance counter of the dynamic schedule
     int64_t* d_Lnn = nullptr;
     std::vector<void*> allocs;
     // execution
@@ -356,6 +357,10 @@ cudaError_t configure(acs_ctx* c, int tpa, int csize)
     c->vis_smem = vis_smem;
     c->xy_smem = xy_smem;
     c->grid = std::min(c->B, ncl) * csize;
+    // more instances than resident clusters: a cluster that finishes takes the
+    // next instance in longest-first order (list scheduling) instead of a
+    // fixed share; results do not depend on which cluster runs an instance
+    c->args.sched = c->B > ncl ? c->d_sched : nullptr;
     c->args.vis_in_smem = vis_smem ? 1 : 0;
     c->args.xy_in_smem = xy_smem ? 1 : 0;
     c->args.vis_global = c->d_vis;
@@ -500,6 +505,7 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     ACS_TRY(dalloc(c, &c->d_stats, 4 * (size_t)B));
     ACS_TRY(dalloc(c, &c->d_P, (size_t)m + 1));
     ACS_TRY(dalloc(c, &c->d_status, 1));
+    ACS_TRY(dalloc(c, &c->d_sched, 1));
     ACS_TRY(dalloc(c, &c->d_Lnn, B));
 
     // decay table P[0] = 1, P[k] = P[k-1]*(1-xi), FP32
@@ -760,6 +766,151 @@ acs_status acs_set_cluster_size(acs_ctx* c, int32_t csize)
 int32_t acs_cluster_size(const acs_ctx* c) { return c ? c->csize : -1; }
 int32_t acs_kernel_mode(const acs_ctx* c) { return c ? c->mode : -1; }
 
+namespace {
+
+// Every mutable array of a context, copied aside (on the context's stream)
+// and put back after each autotuning trial, with the host-side loop state.
+struct Snapshot {
+    struct Buf { void* p; size_t bytes; void* save; };
+    std::vector<Buf> bufs;
+    int64_t iter0 = 0;
+    std::vector<uint8_t> has_best0;
+    bool taken = false;
+
+    Snapshot() = default;
+    Snapshot(const Snapshot&) = delete;
+    Snapshot& operator=(const Snapshot&) = delete;
+    ~Snapshot()
+    {
+        for (Buf& x : bufs) if (x.save) cudaFree(x.save);
+    }
+
+    acs_status take(acs_ctx* c)
+    {
+        size_t tau_n = 0, tour_n = 0, node_n = 0;
+        for (int b = 0; b < c->B; ++b) {
+            const size_t n = (size_t)c->n[b];
+            tau_n += c->p.memory == ACS_MEM_MATRIX ? n * n : n * c->s;
+            tour_n += (size_t)c->m * n;
+            node_n += n;
+        }
+        bufs = {
+            {c->d_tau, sizeof(float) * tau_n, nullptr},
+            {c->d_tours, sizeof(int32_t) * tour_n, nullptr},
+            {c->d_lens, sizeof(int64_t) * (size_t)c->B * c->m, nullptr},
+            {c->d_best, sizeof(int32_t) * node_n, nullptr},
+            {c->d_best_len, sizeof(int64_t) * c->B, nullptr},
+            {c->d_iter, sizeof(int64_t) * c->B, nullptr},
+            {c->d_stats, sizeof(unsigned long long) * 4 * c->B, nullptr},
+        };
+        if (c->p.memory == ACS_MEM_SPM) {
+            bufs.push_back({c->d_spm_idx, sizeof(int32_t) * tau_n, nullptr});
+            bufs.push_back({c->d_spm_tail, sizeof(int32_t) * node_n, nullptr});
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+        // All copies go on the context's stream, in order with the trials: a
+        // device-to-device cudaMemcpy returns before the copy is done and runs
+        // on the legacy stream, which does not order against this one.
+        for (Buf& x : bufs) {
+            if (cudaMalloc(&x.save, x.bytes) != cudaSuccess) {
+                cudaGetLastError();
+                x.save = nullptr;
+                return ACS_ENOMEM;
+            }
+            if (cudaMemcpyAsync(x.save, x.p, x.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                return fail_cuda(c, cudaErrorUnknown);
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+        iter0 = c->iteration;
+        has_best0 = c->has_best;
+        taken = true;
+        return ACS_OK;
+    }
+
+    // puts the state back; nothing to do when take() did not complete (no
+    // trial ran then)
+    acs_status restore(acs_ctx* c)
+    {
+        if (!taken) return ACS_OK;
+        for (Buf& x : bufs)
+            if (cudaMemcpyAsync(x.p, x.save, x.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                return fail_cuda(c, cudaErrorUnknown);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+        c->iteration = iter0;
+        c->has_best = has_best0;
+        c->last_launches = 0;
+        return ACS_OK;
+    }
+};
+
+struct Shape {
+    int tpa, cs;
+    bool res;
+};
+
+// Every launch shape the context can take: (threads per ant, cluster size)
+// and, on the SPM, the global-memory record placement where it differs from
+// the resident one. Leaves the context configured with the last one tried.
+std::vector<Shape> launch_shapes(acs_ctx* c)
+{
+    static const int tpas[4] = {4, 8, 16, 32};
+    static const int css[5] = {1, 2, 4, 8, 16};
+    std::vector<Shape> out;
+    const int nres = c->p.memory == ACS_MEM_SPM ? 2 : 1;
+    for (int ri = 0; ri < nres; ++ri)
+        for (int ci = 0; ci < 5; ++ci)
+            for (int ti = 0; ti < 4; ++ti) {
+                if (css[ci] > c->m) continue;
+                c->spm_resident = ri == 0;
+                if (configure(c, tpas[ti], css[ci]) != cudaSuccess) { cudaGetLastError(); continue; }
+                if (ri == 1 && c->mode != 1) continue;   // nothing new to try
+                out.push_back({tpas[ti], css[ci], ri == 0});
+            }
+    return out;
+}
+
+cudaError_t apply_shape(acs_ctx* c, const Shape& sh)
+{
+    c->spm_resident = sh.res;
+    return configure(c, sh.tpa, sh.cs);
+}
+
+// One trial: every context starts together (the others' streams wait on the
+// first's), runs one warm-up and then `iters` iterations; the group's time is
+// the slowest context's, from the common start.
+acs_status time_group(acs_ctx* const* cs, int k, int iters, float* ms_out)
+{
+    cudaEvent_t e0 = nullptr;
+    std::vector<cudaEvent_t> ends((size_t)k, nullptr);
+    acs_status st = ACS_OK;
+    for (int i = 0; i < k && st == ACS_OK; ++i) st = acs_run_iterations(cs[i], 1);   // captures graphs
+    for (int i = 0; i < k && st == ACS_OK; ++i)
+        if (cudaStreamSynchronize(cs[i]->stream) != cudaSuccess) st = fail_cuda(cs[i], cudaErrorUnknown);
+    if (st == ACS_OK && cudaEventCreate(&e0) != cudaSuccess) st = fail_cuda(cs[0], cudaErrorUnknown);
+    for (int i = 0; i < k && st == ACS_OK; ++i)
+        if (cudaEventCreate(&ends[i]) != cudaSuccess) st = fail_cuda(cs[i], cudaErrorUnknown);
+    if (st == ACS_OK) {
+        cudaEventRecord(e0, cs[0]->stream);
+        for (int i = 1; i < k; ++i) cudaStreamWaitEvent(cs[i]->stream, e0, 0);
+        for (int it = 0; it < iters && st == ACS_OK; ++it)
+            for (int i = 0; i < k && st == ACS_OK; ++i) st = acs_run_iterations(cs[i], 1);
+        float worst = 0.0f;
+        for (int i = 0; i < k && st == ACS_OK; ++i) {
+            cudaEventRecord(ends[i], cs[i]->stream);
+            if (cudaEventSynchronize(ends[i]) != cudaSuccess) { st = fail_cuda(cs[i], cudaErrorUnknown); break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, ends[i]);
+            worst = std::max(worst, ms);
+        }
+        *ms_out = worst;
+    }
+    if (e0) cudaEventDestroy(e0);
+    for (cudaEvent_t e : ends) if (e) cudaEventDestroy(e);
+    return st;
+}
+
+}  // namespace
+
 acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
                         int32_t* chosen_csize)
 {
@@ -770,96 +921,99 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
         if (chosen_csize) *chosen_csize = 1;
         return ACS_OK;
     }
-    // every mutable array of the context, restored after each trial
-    struct Buf { void* p; size_t bytes; void* save; };
-    size_t tau_n = 0, tour_n = 0, node_n = 0;
-    for (int b = 0; b < c->B; ++b) {
-        const size_t n = (size_t)c->n[b];
-        tau_n += c->p.memory == ACS_MEM_MATRIX ? n * n : n * c->s;
-        tour_n += (size_t)c->m * n;
-        node_n += n;
-    }
-    std::vector<Buf> bufs = {
-        {c->d_tau, sizeof(float) * tau_n, nullptr},
-        {c->d_tours, sizeof(int32_t) * tour_n, nullptr},
-        {c->d_lens, sizeof(int64_t) * (size_t)c->B * c->m, nullptr},
-        {c->d_best, sizeof(int32_t) * node_n, nullptr},
-        {c->d_best_len, sizeof(int64_t) * c->B, nullptr},
-        {c->d_iter, sizeof(int64_t) * c->B, nullptr},
-        {c->d_stats, sizeof(unsigned long long) * 4 * c->B, nullptr},
-    };
-    if (c->p.memory == ACS_MEM_SPM) {
-        bufs.push_back({c->d_spm_idx, sizeof(int32_t) * tau_n, nullptr});
-        bufs.push_back({c->d_spm_tail, sizeof(int32_t) * node_n, nullptr});
-    }
-    acs_status st = ACS_OK;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
-    // All copies go on the context's stream, in order with the trials: a
-    // device-to-device cudaMemcpy returns before the copy is done and runs on
-    // the legacy stream, which does not order against this one.
-    for (Buf& x : bufs) {
-        if (cudaMalloc(&x.save, x.bytes) != cudaSuccess) { cudaGetLastError(); st = ACS_ENOMEM; break; }
-        if (cudaMemcpyAsync(x.save, x.p, x.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
-            st = fail_cuda(c, cudaErrorUnknown);
-            break;
-        }
-    }
-    if (st == ACS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail_cuda(c, cudaErrorUnknown);
-    const int64_t iter0 = c->iteration;
-    const std::vector<uint8_t> has_best0 = c->has_best;
-    int best_tpa = c->tpa, best_cs = c->csize;
-    bool best_res = c->spm_resident;
+    Snapshot snap;
+    acs_status st = snap.take(c);
+    Shape best{c->tpa, c->csize, c->spm_resident};
     float best_ms = 0.0f;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (st == ACS_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
-        st = fail_cuda(c, cudaErrorUnknown);
-    const int tpas[4] = {4, 8, 16, 32};
-    const int css[5] = {1, 2, 4, 8, 16};
-    // SPM: records resident in shared memory, or in global memory (smaller
-    // CTAs, more of them per SM)
-    const int nres = c->p.memory == ACS_MEM_SPM ? 2 : 1;
-    for (int ri = 0; ri < nres && st == ACS_OK; ++ri)
-    for (int ci = 0; ci < 5 && st == ACS_OK; ++ci) {
-        for (int ti = 0; ti < 4 && st == ACS_OK; ++ti) {
-            if (css[ci] > c->m) continue;
-            c->spm_resident = ri == 0;
-            if (configure(c, tpas[ti], css[ci]) != cudaSuccess) { cudaGetLastError(); continue; }
-            if (ri == 1 && c->mode != 1) continue;   // nothing new to try
-            st = acs_run_iterations(c, 1);  // warm-up, captures the graph
-            if (st != ACS_OK) break;
-            cudaEventRecord(e0, c->stream);
-            st = acs_run_iterations(c, trial_iters);
-            if (st != ACS_OK) break;
-            cudaEventRecord(e1, c->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail_cuda(c, cudaErrorUnknown); break; }
+    if (st == ACS_OK) {
+        const std::vector<Shape> shapes = launch_shapes(c);
+        for (const Shape& sh : shapes) {
+            if (apply_shape(c, sh) != cudaSuccess) { cudaGetLastError(); continue; }
             float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            st = time_group(&c, 1, trial_iters, &ms);
+            if (st != ACS_OK) break;
             if (best_ms == 0.0f || ms < best_ms) {
                 best_ms = ms;
-                best_tpa = tpas[ti];
-                best_cs = css[ci];
-                best_res = c->spm_resident;
+                best = sh;
             }
-            for (Buf& x : bufs)
-                if (cudaMemcpyAsync(x.p, x.save, x.bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-                    st = fail_cuda(c, cudaErrorUnknown);
-            if (st == ACS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
-                st = fail_cuda(c, cudaErrorUnknown);
-            c->iteration = iter0;
-            c->has_best = has_best0;
+            st = snap.restore(c);
+            if (st != ACS_OK) break;
         }
     }
-    for (Buf& x : bufs) if (x.save) cudaFree(x.save);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    c->iteration = iter0;
-    c->has_best = has_best0;
-    c->last_launches = 0;
-    c->spm_resident = best_res;
-    if (st != ACS_OK) return st;
-    if (configure(c, best_tpa, best_cs) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
-    if (chosen_tpa) *chosen_tpa = best_tpa;
-    if (chosen_csize) *chosen_csize = best_cs;
+    if (st != ACS_OK) {
+        snap.restore(c);
+        return st;
+    }
+    if (apply_shape(c, best) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
+    if (chosen_tpa) *chosen_tpa = best.tpa;
+    if (chosen_csize) *chosen_csize = best.cs;
+    return ACS_OK;
+}
+
+acs_status acs_autotune_group(acs_ctx* const* ctxs, int32_t k, int32_t trial_iters)
+{
+    if (!ctxs || k < 1 || trial_iters < 1) return ACS_EINVAL;
+    for (int i = 0; i < k; ++i) {
+        if (!ctxs[i]) return ACS_EINVAL;
+        for (int j = 0; j < i; ++j) if (ctxs[j] == ctxs[i]) return ACS_EINVAL;
+    }
+    for (int i = 0; i < k; ++i) if (ctxs[i]->poisoned) return ACS_ESTATE;
+    // each context's own choice first
+    for (int i = 0; i < k; ++i) {
+        const acs_status st = acs_autotune(ctxs[i], trial_iters, nullptr, nullptr);
+        if (st != ACS_OK) return st;
+    }
+    if (k == 1) return ACS_OK;
+    std::vector<Snapshot> snaps((size_t)k);
+    std::vector<Shape> cur((size_t)k);
+    std::vector<std::vector<Shape>> shapes((size_t)k);
+    acs_status st = ACS_OK;
+    for (int i = 0; i < k && st == ACS_OK; ++i) {
+        acs_ctx* c = ctxs[i];
+        cur[i] = {c->tpa, c->csize, c->spm_resident};
+        st = snaps[i].take(c);
+        if (st == ACS_OK && !(c->p.flags & ACS_FLAG_RELAXED)) {
+            shapes[i] = launch_shapes(c);
+            if (apply_shape(c, cur[i]) != cudaSuccess) st = fail_cuda(c, cudaErrorUnknown);
+        }
+    }
+    auto restore_all = [&]() -> acs_status {
+        for (int i = 0; i < k; ++i) {
+            const acs_status r = snaps[i].restore(ctxs[i]);
+            if (r != ACS_OK) return r;
+        }
+        return ACS_OK;
+    };
+    float best_ms = 0.0f;
+    if (st == ACS_OK) st = time_group(ctxs, k, trial_iters, &best_ms);
+    if (st == ACS_OK) st = restore_all();
+    // coordinate descent: one context's shape at a time, the others fixed,
+    // every trial timed with the whole group running; two passes at most
+    for (int pass = 0; pass < 2 && st == ACS_OK; ++pass) {
+        bool improved = false;
+        for (int i = 0; i < k && st == ACS_OK; ++i) {
+            for (const Shape& sh : shapes[i]) {
+                if (sh.tpa == cur[i].tpa && sh.cs == cur[i].cs && sh.res == cur[i].res) continue;
+                if (apply_shape(ctxs[i], sh) != cudaSuccess) { cudaGetLastError(); continue; }
+                float ms = 0.0f;
+                st = time_group(ctxs, k, trial_iters, &ms);
+                if (st == ACS_OK) st = restore_all();
+                if (st != ACS_OK) break;
+                if (ms < 0.995f * best_ms) {   // beyond the trial-to-trial noise
+                    best_ms = ms;
+                    cur[i] = sh;
+                    improved = true;
+                }
+            }
+            if (st == ACS_OK && apply_shape(ctxs[i], cur[i]) != cudaSuccess)
+                st = fail_cuda(ctxs[i], cudaErrorUnknown);
+        }
+        if (!improved) break;
+    }
+    if (st != ACS_OK) {
+        restore_all();
+        return st;
+    }
     return ACS_OK;
 }
 

@@ -56,6 +56,8 @@ struct Misc {
     long long best_len;
     long long iteration;
     int nrel;                     // edges this CTA writes in the current step
+    int next;                     // the cluster's next instance (drawn by rank 0)
+    int next_local;               // this CTA's copy of rank 0's draw
 };
 
 __device__ __forceinline__ bool visited(const uint32_t* vis, int j)
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     const int s_slots = A.s;
 
-    for (int oi = cid; oi < A.num_inst; oi += ncl) {
+    for (int oi = cid; oi < A.num_inst;) {
         const int b = A.order[oi];
         const InstDesc D = A.desc[b];
         const int n = D.n, cl = D.cl, W = D.W;
@@ -914,6 +916,22 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
             }
         }
         cluster.sync();
+        // The first ncl instances (longest first) go to clusters 0..ncl-1; with
+        // a counter, a cluster that finishes then takes the next untaken
+        // instance. Rank 0 draws it; each CTA's thread 0 copies it from rank
+        // 0's shared memory between two cluster barriers (the second keeps
+        // rank 0 from rewriting it or exiting before every CTA has read it),
+        // and the CTA reads its own copy, a load the compiler keeps
+        // warp-uniform, so the instance's values stay in uniform registers.
+        if (A.sched) {
+            if (rank == 0 && tid == 0) misc->next = ncl + atomicAdd(A.sched, 1);
+            cluster.sync();
+            if (tid == 0) misc->next_local = cluster.map_shared_rank(misc, 0)->next;
+            cluster.sync();
+            oi = misc->next_local;
+        } else {
+            oi += ncl;
+        }
     }
 }
 
@@ -990,12 +1008,17 @@ int construct_occupancy(int tpa, int mode, int block, size_t smem, int csize)
 }
 
 // Stream-ordered launch of one iteration on clusters of `csize` CTAs; safe
-// inside a stream capture. grid must be a multiple of csize.
+// inside a stream capture (the counter reset becomes a memset node). grid
+// must be a multiple of csize.
 cudaError_t launch_construct(const ConstructArgs& A, int tpa, int mode, int grid, int block,
                              size_t smem, int csize, cudaStream_t stream)
 {
     void* k = select_kernel(tpa, mode);
     if (!k) return cudaErrorInvalidValue;
+    if (A.sched) {
+        const cudaError_t e = cudaMemsetAsync(A.sched, 0, sizeof(int32_t), stream);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);

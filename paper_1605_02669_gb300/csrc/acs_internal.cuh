@@ -58,6 +58,9 @@ struct ConstructArgs {
     int32_t mc;               // ants per CTA of a cluster = ceil(m / cluster size)
     int32_t nrec;             // SPM records per CTA in shared memory (0 = global)
     int32_t skip_default;     // SPM: a local update of an absent edge inserts nothing
+    int32_t* sched;           // next-instance counter (zeroed before each launch) when the
+                              // batch has more instances than resident clusters; null =
+                              // cluster k takes instances k, k + clusters, ...
 };
 
 // Shared-memory carve of the construct kernel; the same arithmetic runs on

@@ -100,6 +100,10 @@ def test_null_context_calls(lib):
     assert lib.acs_set_cluster_size(None, 2) == acs.ACS_EINVAL
     assert lib.acs_set_threads_per_ant(None, 8) == acs.ACS_EINVAL
     assert lib.acs_autotune(None, 1, None, None) == acs.ACS_EINVAL
+    assert lib.acs_autotune_group(None, 2, 1) == acs.ACS_EINVAL
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert lib.acs_autotune_group(nulls, 2, 1) == acs.ACS_EINVAL
+    assert lib.acs_autotune_group(nulls, 0, 1) == acs.ACS_EINVAL
     lib.acs_destroy(None)
 
 

@@ -320,6 +320,52 @@ def test_autotune_on_fresh_batch_then_parity(oracle_mod):
         assert_same_state(gpu, r, 0, b)
 
 
+@pytest.mark.parametrize("memory", [0, 1])
+def test_dynamic_instance_schedule_parity(oracle_mod, memory):
+    # 400 instances on 1024-thread CTAs (32 lanes x 32 ants, one cluster of
+    # one CTA per instance): at most one CTA per SM is resident, so the
+    # clusters take instances from the counter after the first wave
+    rng = np.random.default_rng(31)
+    sizes = [int(x) for x in rng.integers(20, 90, 400)]
+    xy, off = instances.batch(sizes, ["uniform", "clustered"] * 200, seed=17)
+    kw = dict(m=32, cl=16, memory=memory, spm_slots=4, seed=5)
+    gpu = acs.Colony(xy, acs.params(**kw), offsets=off)
+    gpu.set_cluster_size(1)
+    gpu.set_threads_per_ant(32)
+    assert gpu.cluster_size == 1 and gpu.threads_per_ant == 32
+    gpu.run(2)
+    for b in range(len(sizes)):
+        r = oracle.Colony(xy[off[b]:off[b + 1]], oracle.make_params(**kw), instance=b)
+        r.run(2)
+        assert_same_state(gpu, r, memory, b)
+
+
+def test_group_autotune_keeps_state(oracle_mod):
+    import torch
+
+    sizes = [150, 320, 90, 260, 200, 120]
+    xy, off = instances.batch(sizes, ["uniform", "clustered"] * 3, seed=23)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    cols, kws = [], []
+    for memory, st in zip((0, 1), streams):
+        kw = dict(m=32, cl=16, memory=memory, spm_slots=8, seed=3)
+        c = acs.Colony(xy, acs.params(**kw), offsets=off)
+        c.set_stream(st.cuda_stream)
+        c.run(1)
+        cols.append(c)
+        kws.append(kw)
+    acs.autotune_group(cols, trial_iters=1)
+    for c in cols:
+        assert c.iteration == 1
+        c.run(2)
+    torch.cuda.synchronize()
+    for c, kw in zip(cols, kws):
+        for b in range(len(sizes)):
+            r = oracle.Colony(xy[off[b]:off[b + 1]], oracle.make_params(**kw), instance=b)
+            r.run(3)
+            assert_same_state(c, r, kw["memory"], b)
+
+
 def test_repeatable_bits(oracle_mod):
     xy = instances.clustered(400, seed=6)
     runs = []
