@@ -381,10 +381,12 @@ def cpu_baseline_leg(seconds_budget=15.0):
 KERNEL_SOURCES = ["acs_construct.cu", "acs_device.cuh", "acs_internal.cuh"]
 # DRAM bytes (read + write) of one construct launch of this workload, from one
 # ncu capture each (profiles/), keyed by (memory, threads per ant, cluster
-# size) and valid only for the kernel sources they were taken on.
+# size, kernel variant) and valid only for the kernel sources they were taken on.
 CAPTURED_TRAFFIC = {
-    ("paper", "matrix", 32, 16): {"bytes": 36760832 + 377344, "sources": "4ef0eeb2e550"},
-    ("paper", "spm", 32, 16): {"bytes": 16442624 + 0, "sources": "4ef0eeb2e550"},
+    ("paper", "matrix", 32, 16, 0): {"bytes": 36762880 + 395264, "sources": "6456c4f0e998"},
+    ("paper", "spm", 32, 16, 2): {"bytes": 16444160 + 0, "sources": "6456c4f0e998"},
+    ("batch256", "matrix", 8, 1, 0): {"bytes": 40310618368 + 1241047552, "sources": "6456c4f0e998"},
+    ("batch256", "spm", 8, 1, 1): {"bytes": 4616091904 + 273832704, "sources": "6456c4f0e998"},
 }
 
 
@@ -398,8 +400,8 @@ def kernel_sources_digest():
     return h.hexdigest()[:12]
 
 
-def kernel_traffic(memory, tpa, csize):
-    rec = CAPTURED_TRAFFIC.get((WORKLOAD, memory, tpa, csize))
+def kernel_traffic(memory, tpa, csize, mode):
+    rec = CAPTURED_TRAFFIC.get((WORKLOAD, memory, tpa, csize, mode))
     if rec is None or rec["sources"] != kernel_sources_digest():
         return None
     return rec["bytes"]
@@ -864,7 +866,7 @@ def run_ours(args, rank, world, local):
         roofs.append({
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": kernel_traffic(name, t["threads_per_ant"], t["cluster_size"]),
+            "traffic": kernel_traffic(name, t["threads_per_ant"], t["cluster_size"], t["kernel_mode"]),
             "kernel": "construct_kernel<%d,%d> (%s, %d instances in one launch, clusters of %d)"
                       % (t["threads_per_ant"], col.kernel_mode, name, len(sizes),
                          t["cluster_size"]),
