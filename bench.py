@@ -764,10 +764,9 @@ def run_ours(args, rank, world, local):
     tuning = {}
     mems = {"both": WORKLOADS[WORKLOAD]["memories"], "matrix": (acs.ACS_MEM_MATRIX,),
             "spm": (acs.ACS_MEM_SPM,)}[args.only]
-    # joint tuning of the concurrent colonies, except on large16, where one
-    # trial iteration takes about a second and the joint passes would add
-    # minutes of set-up
-    group_tune = len(mems) > 1 and WORKLOAD != "large16"
+    # joint tuning of the concurrent colonies (one trial iteration on large16,
+    # where an iteration takes most of a second)
+    group_tune = len(mems) > 1
     for mem, st in zip(mems if sizes else (), (sA, sB)):
         p = acs.params(m=M, cl=CL, beta=2, q0=0.9, rho=0.1, xi=0.1, memory=mem, spm_slots=8,
                        seed=seed)
@@ -788,7 +787,7 @@ def run_ours(args, rank, world, local):
     if group_tune and ctxs and not (args.tpa or args.cluster):
         # the colonies run concurrently and compete for the SMs: their shapes
         # are tuned together (each alone first, then jointly)
-        acs.autotune_group([c for c, _ in ctxs], trial_iters=2)
+        acs.autotune_group([c for c, _ in ctxs], trial_iters=1 if WORKLOAD == "large16" else 2)
     for (col, _), mem in zip(ctxs, mems):
         tuning[MEM_NAMES[mem]] = {"threads_per_ant": col.threads_per_ant,
                                   "cluster_size": col.cluster_size,

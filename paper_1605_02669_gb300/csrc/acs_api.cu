@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <utility>
 #include <vector>
 
 #include "acs.h"
@@ -911,16 +912,12 @@ acs_status time_group(acs_ctx* const* cs, int k, int iters, float* ms_out)
 
 }  // namespace
 
-acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
-                        int32_t* chosen_csize)
+namespace {
+
+// Times every launch shape of the context alone (state restored after each
+// trial), applies the fastest and returns each shape's time in `timed`.
+acs_status tune_alone(acs_ctx* c, int32_t trial_iters, std::vector<std::pair<Shape, float>>* timed)
 {
-    if (!c || trial_iters < 1) return ACS_EINVAL;
-    if (c->poisoned) return ACS_ESTATE;
-    if (c->p.flags & ACS_FLAG_RELAXED) {   // one launch shape only
-        if (chosen_tpa) *chosen_tpa = 32;
-        if (chosen_csize) *chosen_csize = 1;
-        return ACS_OK;
-    }
     Snapshot snap;
     acs_status st = snap.take(c);
     Shape best{c->tpa, c->csize, c->spm_resident};
@@ -932,6 +929,7 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
             float ms = 0.0f;
             st = time_group(&c, 1, trial_iters, &ms);
             if (st != ACS_OK) break;
+            if (timed) timed->push_back({sh, ms});
             if (best_ms == 0.0f || ms < best_ms) {
                 best_ms = ms;
                 best = sh;
@@ -945,8 +943,25 @@ acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
         return st;
     }
     if (apply_shape(c, best) != cudaSuccess) return fail_cuda(c, cudaErrorUnknown);
-    if (chosen_tpa) *chosen_tpa = best.tpa;
-    if (chosen_csize) *chosen_csize = best.cs;
+    return ACS_OK;
+}
+
+}  // namespace
+
+acs_status acs_autotune(acs_ctx* c, int32_t trial_iters, int32_t* chosen_tpa,
+                        int32_t* chosen_csize)
+{
+    if (!c || trial_iters < 1) return ACS_EINVAL;
+    if (c->poisoned) return ACS_ESTATE;
+    if (c->p.flags & ACS_FLAG_RELAXED) {   // one launch shape only
+        if (chosen_tpa) *chosen_tpa = 32;
+        if (chosen_csize) *chosen_csize = 1;
+        return ACS_OK;
+    }
+    const acs_status st = tune_alone(c, trial_iters, nullptr);
+    if (st != ACS_OK) return st;
+    if (chosen_tpa) *chosen_tpa = c->tpa;
+    if (chosen_csize) *chosen_csize = c->csize;
     return ACS_OK;
 }
 
@@ -958,24 +973,27 @@ acs_status acs_autotune_group(acs_ctx* const* ctxs, int32_t k, int32_t trial_ite
         for (int j = 0; j < i; ++j) if (ctxs[j] == ctxs[i]) return ACS_EINVAL;
     }
     for (int i = 0; i < k; ++i) if (ctxs[i]->poisoned) return ACS_ESTATE;
-    // each context's own choice first
+    // each context's own choice first; the joint passes then try only the
+    // shapes that ran within twice the context's best time alone
+    std::vector<std::vector<Shape>> shapes((size_t)k);
     for (int i = 0; i < k; ++i) {
-        const acs_status st = acs_autotune(ctxs[i], trial_iters, nullptr, nullptr);
+        if (ctxs[i]->p.flags & ACS_FLAG_RELAXED) continue;   // one launch shape only
+        std::vector<std::pair<Shape, float>> timed;
+        const acs_status st = tune_alone(ctxs[i], trial_iters, &timed);
         if (st != ACS_OK) return st;
+        float best = 0.0f;
+        for (const auto& t : timed) best = best == 0.0f ? t.second : std::min(best, t.second);
+        for (const auto& t : timed)
+            if (t.second <= 2.0f * best) shapes[i].push_back(t.first);
     }
     if (k == 1) return ACS_OK;
     std::vector<Snapshot> snaps((size_t)k);
     std::vector<Shape> cur((size_t)k);
-    std::vector<std::vector<Shape>> shapes((size_t)k);
     acs_status st = ACS_OK;
     for (int i = 0; i < k && st == ACS_OK; ++i) {
         acs_ctx* c = ctxs[i];
         cur[i] = {c->tpa, c->csize, c->spm_resident};
         st = snaps[i].take(c);
-        if (st == ACS_OK && !(c->p.flags & ACS_FLAG_RELAXED)) {
-            shapes[i] = launch_shapes(c);
-            if (apply_shape(c, cur[i]) != cudaSuccess) st = fail_cuda(c, cudaErrorUnknown);
-        }
     }
     auto restore_all = [&]() -> acs_status {
         for (int i = 0; i < k; ++i) {
