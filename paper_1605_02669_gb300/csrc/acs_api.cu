@@ -192,6 +192,92 @@ __global__ void hw_kernel(const InstDesc* desc, const int32_t* xy, float* hw, in
     }
 }
 
+// Bitonic network on keys[0..N) in shared memory, largest first, by the
+// CTA's 256 threads (N = 256 or 512).
+template <int N>
+__device__ void sort_desc(unsigned long long* keys)
+{
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += 256) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = keys[i], b = keys[ixj];
+                    if (((i & k) == 0) ? (a < b) : (a > b)) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// SPM extended neighbour lists. For node c: the kExtList nodes j != c with
+// the largest full-scan keys pack_pj(tau0 * eta(c, j)^beta, j) of an absent
+// trail, largest first (-1 padded when n - 1 < kExtList). Every trail absent
+// from a record is tau0 (Sec. 3.2), so the first unvisited node of this list
+// is the full scan's choice among absent trails (Alg. 2); the construct
+// kernel compares it with the record's entries and scans all n nodes only
+// when every listed node is visited. One CTA of 256 threads per node: a
+// sorted top list, refreshed from a buffer of the keys that beat its last
+// entry (bitonic sort and merge).
+__global__ void __launch_bounds__(256) ext_list_kernel(const InstDesc* desc, const int32_t* xy,
+                                                       int32_t* ext, int beta)
+{
+    __shared__ unsigned long long top[kExtList];
+    __shared__ unsigned long long buf[2 * kExtList];
+    __shared__ int cnt;
+    const InstDesc D = desc[blockIdx.y];
+    const int n = D.n, t = threadIdx.x;
+    const int2* p = reinterpret_cast<const int2*>(xy) + D.xy_off;
+    auto key_of = [&](int c, int j) -> unsigned long long {
+        if (j == c || j >= n) return 0ull;
+        return pack_pj(__fmul_rn(D.tau0, heuristic(euc2d(p[c], p[j]), beta)), j);
+    };
+    for (int c = blockIdx.x; c < n; c += gridDim.x) {
+        top[t] = key_of(c, t);
+        if (t == 0) cnt = 0;
+        __syncthreads();
+        sort_desc<kExtList>(top);
+        for (int j0 = kExtList; j0 < n; j0 += 256) {
+            const unsigned long long thr = top[kExtList - 1];
+            const unsigned long long k = key_of(c, j0 + t);
+            if (k > thr) buf[atomicAdd(&cnt, 1)] = k;
+            __syncthreads();
+            const int nb = cnt;
+            __syncthreads();   // every thread has read cnt before it changes again
+            if (nb >= kExtList || (j0 + 256 >= n && nb > 0)) {
+                for (int i = nb + t; i < 2 * kExtList; i += 256) buf[i] = 0ull;
+                __syncthreads();
+                sort_desc<2 * kExtList>(buf);
+                // the kExtList largest of both sorted lists form a bitonic
+                // sequence: the larger of top[i] and buf[kExtList - 1 - i]
+                const unsigned long long a = top[t], b = buf[kExtList - 1 - t];
+                __syncthreads();
+                top[t] = a > b ? a : b;
+                if (t == 0) cnt = 0;
+                __syncthreads();
+                for (int j = kExtList >> 1; j > 0; j >>= 1) {
+                    const int ixj = t ^ j;
+                    if (ixj > t) {
+                        const unsigned long long x = top[t], y = top[ixj];
+                        if (x < y) {
+                            top[t] = y;
+                            top[ixj] = x;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        const unsigned long long k = top[t];
+        ext[((size_t)D.row_off + c) * kExtList + t] = k ? (int32_t)(0xffffffffu - (uint32_t)k) : -1;
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ context
 
 struct acs_ctx {
@@ -208,6 +294,7 @@ struct acs_ctx {
     int32_t* d_nn = nullptr;
     float* d_w = nullptr;
     float* d_hw = nullptr;
+    int32_t* d_ext = nullptr;    // SPM extended neighbour lists [rows][kExtList]
     float* d_tau = nullptr;
     int32_t* d_spm_idx = nullptr;
     int32_t* d_spm_tail = nullptr;
@@ -230,6 +317,7 @@ struct acs_ctx {
     cudaGraphExec_t exec = nullptr;
     ConstructArgs args{};
     int tpa = 8, grid = 1, block = 256, sms = 1, csize = 1, max_smem = 0, mode = 0;
+    int variant = 0;   // mode, plus kExtVariant when the SPM kernel uses the extended lists
     bool vis_smem = true, xy_smem = false;
     bool spm_resident = true;   // SPM records in shared memory when they fit
     size_t smem = 0;
@@ -347,12 +435,18 @@ cudaError_t configure(acs_ctx* c, int tpa, int csize)
     block = (block + 31) / 32 * 32;
     if (block < m) return cudaErrorInvalidConfiguration;
     const int mode = !spm ? 0 : (nrec > 0 ? 2 : 1);
-    ACS_TRY(prepare_construct(tpa, mode, L.total));
-    const int ncl = construct_occupancy(tpa, mode, block, L.total, csize);
+    // the SPM variant with the extended lists when some instance's full scan
+    // would deal each warp of a CTA more than two 128-node items (the kernel
+    // applies the same test per instance)
+    const bool ext = spm && c->d_ext && ((c->max_n + 127) >> 7) > 2 * (block >> 5);
+    const int variant = mode + (ext ? kExtVariant : 0);
+    ACS_TRY(prepare_construct(tpa, variant, L.total));
+    const int ncl = construct_occupancy(tpa, variant, block, L.total, csize);
     if (ncl < 1) return cudaErrorInvalidConfiguration;
     c->tpa = tpa;
     c->csize = csize;
     c->mode = mode;
+    c->variant = variant;
     c->block = block;
     c->smem = L.total;
     c->vis_smem = vis_smem;
@@ -410,6 +504,7 @@ cudaError_t plan_launch(acs_ctx* c)
     A.nn = c->d_nn;
     A.w = c->d_w;
     A.hw = c->d_hw;
+    A.ext = c->d_ext;
     A.tau = c->d_tau;
     A.spm_idx = c->d_spm_idx;
     A.spm_tail = c->d_spm_tail;
@@ -497,6 +592,7 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     if (c->p.memory == ACS_MEM_SPM) {
         ACS_TRY(dalloc(c, &c->d_spm_idx, tau_total));
         ACS_TRY(dalloc(c, &c->d_spm_tail, (size_t)total_n));
+        ACS_TRY(dalloc(c, &c->d_ext, (size_t)kExtList * total_n));
     }
     ACS_TRY(dalloc(c, &c->d_tours, tour_total));
     ACS_TRY(dalloc(c, &c->d_lens, (size_t)B * m));
@@ -532,6 +628,11 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     const size_t vis_bytes = sizeof(uint32_t) * ((c->max_n + 31) / 32);
     nn_tour_kernel<<<B, 32, vis_bytes, st>>>(c->d_desc, c->d_xy, c->d_nn, c->d_Lnn);
     ACS_TRY(cudaGetLastError());
+    if (c->d_ext) {   // needs tau0, which the tour kernel stored in the descriptors
+        ext_list_kernel<<<dim3(std::min(c->max_n, 4096), B), 256, 0, st>>>(c->d_desc, c->d_xy, c->d_ext,
+                                                                           c->p.beta);
+        ACS_TRY(cudaGetLastError());
+    }
     dim3 ig(256, B);
     if (c->d_hw) {
         hw_kernel<<<dim3(1024, B), 256, 0, st>>>(c->d_desc, c->d_xy, c->d_hw, c->p.beta);
@@ -701,7 +802,7 @@ acs_status acs_run_iterations(acs_ctx* c, int32_t iters)
         if (e != cudaSuccess) return fail_cuda(c, e);
         cudaError_t le = (c->p.flags & ACS_FLAG_RELAXED)
                              ? launch_relaxed(c->args, c->B, (c->max_n + 31) / 32, c->stream)
-                             : launch_construct(c->args, c->tpa, c->mode, c->grid, c->block,
+                             : launch_construct(c->args, c->tpa, c->variant, c->grid, c->block,
                                                 c->smem, c->csize, c->stream);
         e = cudaStreamEndCapture(c->stream, &c->graph);
         if (le != cudaSuccess) return fail_cuda(c, le);
@@ -1002,32 +1103,65 @@ acs_status acs_autotune_group(acs_ctx* const* ctxs, int32_t k, int32_t trial_ite
         }
         return ACS_OK;
     };
-    float best_ms = 0.0f;
-    if (st == ACS_OK) st = time_group(ctxs, k, trial_iters, &best_ms);
-    if (st == ACS_OK) st = restore_all();
-    // coordinate descent: one context's shape at a time, the others fixed,
-    // every trial timed with the whole group running; two passes at most
-    for (int pass = 0; pass < 2 && st == ACS_OK; ++pass) {
-        bool improved = false;
-        for (int i = 0; i < k && st == ACS_OK; ++i) {
-            for (const Shape& sh : shapes[i]) {
-                if (sh.tpa == cur[i].tpa && sh.cs == cur[i].cs && sh.res == cur[i].res) continue;
-                if (apply_shape(ctxs[i], sh) != cudaSuccess) { cudaGetLastError(); continue; }
-                float ms = 0.0f;
-                st = time_group(ctxs, k, trial_iters, &ms);
-                if (st == ACS_OK) st = restore_all();
-                if (st != ACS_OK) break;
-                if (ms < 0.995f * best_ms) {   // beyond the trial-to-trial noise
-                    best_ms = ms;
-                    cur[i] = sh;
-                    improved = true;
-                }
-            }
-            if (st == ACS_OK && apply_shape(ctxs[i], cur[i]) != cudaSuccess)
-                st = fail_cuda(ctxs[i], cudaErrorUnknown);
+    // Coordinate descent (one context's shape at a time, the others fixed,
+    // every trial timed with the whole group running; two passes at most)
+    // from two starts: the shapes best alone, and each context's smallest
+    // shape (fewest lanes x CTAs per instance, records in global memory
+    // first), which leaves room on the SMs for the others. The better end
+    // point is kept.
+    auto apply_all = [&](const std::vector<Shape>& sh) -> acs_status {
+        for (int i = 0; i < k; ++i) {
+            if (ctxs[i]->p.flags & ACS_FLAG_RELAXED) continue;
+            if (apply_shape(ctxs[i], sh[i]) != cudaSuccess) return fail_cuda(ctxs[i], cudaErrorUnknown);
         }
-        if (!improved) break;
+        return ACS_OK;
+    };
+    auto descend = [&](std::vector<Shape>& at, float* ms_out) -> acs_status {
+        acs_status r = apply_all(at);
+        float best_ms = 0.0f;
+        if (r == ACS_OK) r = time_group(ctxs, k, trial_iters, &best_ms);
+        if (r == ACS_OK) r = restore_all();
+        for (int pass = 0; pass < 2 && r == ACS_OK; ++pass) {
+            bool improved = false;
+            for (int i = 0; i < k && r == ACS_OK; ++i) {
+                for (const Shape& sh : shapes[i]) {
+                    if (sh.tpa == at[i].tpa && sh.cs == at[i].cs && sh.res == at[i].res) continue;
+                    if (apply_shape(ctxs[i], sh) != cudaSuccess) { cudaGetLastError(); continue; }
+                    float ms = 0.0f;
+                    r = time_group(ctxs, k, trial_iters, &ms);
+                    if (r == ACS_OK) r = restore_all();
+                    if (r != ACS_OK) break;
+                    if (ms < 0.99f * best_ms) {   // 1 %: beyond the trial-to-trial noise
+                        best_ms = ms;
+                        at[i] = sh;
+                        improved = true;
+                    }
+                }
+                if (r == ACS_OK && !(ctxs[i]->p.flags & ACS_FLAG_RELAXED) &&
+                    apply_shape(ctxs[i], at[i]) != cudaSuccess)
+                    r = fail_cuda(ctxs[i], cudaErrorUnknown);
+            }
+            if (!improved) break;
+        }
+        *ms_out = best_ms;
+        return r;
+    };
+    std::vector<Shape> small = cur;
+    for (int i = 0; i < k; ++i) {
+        for (const Shape& sh : shapes[i]) {
+            const Shape& b = small[i];
+            const int fs = sh.tpa * sh.cs, fb = b.tpa * b.cs;
+            if (fs < fb || (fs == fb && !sh.res && b.res)) small[i] = sh;
+        }
     }
+    float ms_a = 0.0f, ms_b = 0.0f;
+    std::vector<Shape> end_a = cur, end_b = small;
+    if (st == ACS_OK) st = descend(end_a, &ms_a);
+    bool same_start = true;
+    for (int i = 0; i < k; ++i)
+        same_start &= small[i].tpa == cur[i].tpa && small[i].cs == cur[i].cs && small[i].res == cur[i].res;
+    if (st == ACS_OK && !same_start) st = descend(end_b, &ms_b);
+    if (st == ACS_OK) st = apply_all(!same_start && ms_b < ms_a ? end_b : end_a);
     if (st != ACS_OK) {
         restore_all();
         return st;

@@ -122,14 +122,6 @@ __device__ __forceinline__ unsigned group_mask(int lane)
     else return ((1u << TPA) - 1u) << (lane & ~(TPA - 1));
 }
 
-// (product bits, node) packed so that the larger product wins and, among
-// equal products, the lower node index.
-__device__ __forceinline__ unsigned long long pack_pj(float p, int j)
-{
-    return ((unsigned long long)__float_as_uint(p) << 32) |
-           (unsigned long long)(0xffffffffu - (uint32_t)j);
-}
-
 // Warp maximum of the packed keys: the largest high word (product bits) by a
 // hardware reduction, then the largest low word among the lanes that hold it.
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k)
@@ -216,10 +208,15 @@ __device__ __forceinline__ void prefetch_l1(const void* p)
 // record r resident, for the launch, in the shared memory of CTA r mod C
 // (loaded at the start, written back after the global update); other CTAs
 // read it through distributed shared memory.
-template <int TPA, int MODE>
+// EXT (SPM only): empty candidate sets are settled from the extended
+// neighbour lists where a full scan would be long (a separate variant, so that
+// the launches that never use the lists keep the register allocation of the
+// plain kernel).
+template <int TPA, int MODE, bool EXT>
 __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs A)
 {
     constexpr bool SPM = MODE != 0;
+    static_assert(!EXT || SPM, "the extended lists serve the SPM only");
     constexpr bool RG = MODE == 1;   // SPM record loads go through L2
     constexpr int V = 32 / TPA;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -266,6 +263,7 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         int* ev0 = (int*)(smem + L.ev0);
         int* ev1 = (int*)(smem + L.ev1);
         Misc* misc = (Misc*)(smem + L.misc);
+        int* s_xj = (int*)(smem + L.xj);   // an ant's list node, when its candidates are visited
         int32_t* ridx_s = (int32_t*)(smem + L.ridx);
         float* rval_s = (float*)(smem + L.rval);
         int32_t* rtail_s = (int32_t*)(smem + L.rtail);
@@ -280,6 +278,8 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         int32_t* sidx = A.spm_idx + D.tau_off;    // SPM only
         int32_t* stail = A.spm_tail + D.node_off; // SPM only
         int32_t* tours = A.tours + D.tour_off;
+        // SPM: extended neighbour lists of this instance (null = full scans only)
+        const int32_t* ext_rows = (EXT && A.ext) ? A.ext + (size_t)kExtList * D.row_off : nullptr;
         int32_t* best = A.best + D.node_off;
 
         // SPM record r: this CTA's shared copy, another CTA's through DSMEM, or global
@@ -368,6 +368,36 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
             }
             const unsigned anyb = __ballot_sync(gmask, lane_any) & gmask;
             if (anyb != 0u) return true;
+            if constexpr (EXT) {
+                // the list path only where a full scan would deal each of the
+                // CTA's warps more than two 128-node items: shorter scans end
+                // sooner than the list path's dependent loads
+                if (ext_rows && ((n + 127) >> 7) > 2 * (nthr >> 5)) {
+                    // the candidate set is empty: the first unvisited node of
+                    // the extended list (static data and this ant's own visited
+                    // bits, so it is found inside the barrier) stands for every
+                    // absent trail of the full scan; choose() weighs it against
+                    // the record's entries after the barrier
+                    const int32_t* xrow = ext_rows + (size_t)c * kExtList;
+                    constexpr int NE = 8;
+                    int js = -1;
+                    for (int b0 = 0; b0 < kExtList && js < 0; b0 += NE * TPA) {
+                        int e[NE];
+#pragma unroll
+                        for (int i = 0; i < NE; ++i) e[i] = __ldg(xrow + b0 + i * TPA + gl);
+#pragma unroll
+                        for (int i = 0; i < NE; ++i) {
+                            const bool u = e[i] >= 0 && !visited(vis, e[i]);
+                            const unsigned bu = __ballot_sync(gmask, u) & gmask;
+                            if (bu != 0u && js < 0) js = __shfl_sync(gmask, e[i], __ffs(bu) - 1 - gbase, TPA);
+                        }
+                    }
+                    if (js >= 0) {
+                        if (gl == 0) s_xj[al] = js;
+                        return true;
+                    }
+                }
+            }
             if (gl == 0) {
                 const int qi = atomicAdd(&misc->qn[stp & 1], 1);
                 qant[qi] = al;
@@ -386,6 +416,53 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         auto choose = [&](int stp, int al, int c, const int (&nv)[V], const float (&wv)[V],
                           const bool (&unv)[V], const uint4& x) {
             const int a = a0 + al;
+            if constexpr (EXT) {
+                bool lane_any = false;
+#pragma unroll
+                for (int i = 0; i < V; ++i) lane_any |= unv[i];
+                if (ext_rows && (__ballot_sync(gmask, lane_any) & gmask) == 0u) {
+                    // Alg. 2's full scan, resolved by the extended list: the
+                    // largest key among the list's first unvisited node (trail
+                    // tau0) and the record's unvisited entries (stored trails)
+                    const int js = s_xj[al];
+                    const uint32_t* vis = vis_base + (size_t)al * W;
+                    const float* hrow = hw ? hw + (size_t)c * n : nullptr;
+                    const int2 pc = xy[c];
+                    unsigned long long key = 0ull;
+                    if (gl == 0) {
+                        const float h = hrow ? __ldg(hrow + js) : heuristic(euc2d(pc, xy[js]), A.beta);
+                        key = pack_pj(__fmul_rn(tau0, h), js);
+                    }
+                    const Rec R = rec(c);
+                    for (int q = gl; q < s_slots; q += TPA) {
+                        const int oj = ld_i<RG>(R.idx + q);
+                        const float ot = ld_f<RG>(R.val + q);
+                        if (oj >= 0 && !visited(vis, oj)) {
+                            const float hj = hrow ? __ldg(hrow + oj) : heuristic(euc2d(pc, xy[oj]), A.beta);
+                            const unsigned long long k2 = pack_pj(__fmul_rn(ot, hj), oj);
+                            key = k2 > key ? k2 : key;
+                        }
+                    }
+                    if constexpr (TPA == 32) {
+                        key = warp_max_u64(key);
+                    } else {
+#pragma unroll
+                        for (int off = TPA / 2; off >= 1; off >>= 1) {
+                            const unsigned long long o = __shfl_xor_sync(gmask, key, off, TPA);
+                            key = o > key ? o : key;
+                        }
+                    }
+                    const int next = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+                    if (gl == 0) {
+                        nodeb[stp & 1][al] = next;
+                        pedge[al] = ((uint32_t)c << 16) | (uint32_t)next;
+                        tours[(size_t)a * n + stp] = next;
+                        vis_base[(size_t)al * W + (next >> 5)] |= 1u << (next & 31);
+                        atomicAdd(&misc->stat[0], 1ull);   // a full-scan selection
+                    }
+                    return;
+                }
+            }
             float tv[V];
             if constexpr (!SPM) {
                 const float* trow = tau + (size_t)c * n;
@@ -906,7 +983,8 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
         }
         if (tid == 0) {
             unsigned long long* st = A.stats + 4 * (size_t)b;
-            atomicAdd(st + 0, n_fb);
+            if constexpr (EXT) atomicAdd(st + 0, n_fb + misc->stat[0]);
+            else atomicAdd(st + 0, n_fb);
             if (rank == 0) atomicAdd(st + 1, (unsigned long long)m * (unsigned long long)(n - 1));
             atomicAdd(st + 2, misc->stat[2]);
             atomicAdd(st + 3, misc->stat[3]);
@@ -935,30 +1013,34 @@ __global__ void __launch_bounds__(1024, 1) construct_kernel(const ConstructArgs 
     }
 }
 
-template <int TPA, int MODE>
+template <int TPA, int MODE, bool EXT>
 static void* kernel_ptr()
 {
-    return reinterpret_cast<void*>(construct_kernel<TPA, MODE>);
+    return reinterpret_cast<void*>(construct_kernel<TPA, MODE, EXT>);
 }
 
-template <int MODE>
+template <int MODE, bool EXT>
 static void* select_tpa(int tpa)
 {
     switch (tpa) {
-    case 4: return kernel_ptr<4, MODE>();
-    case 8: return kernel_ptr<8, MODE>();
-    case 16: return kernel_ptr<16, MODE>();
-    case 32: return kernel_ptr<32, MODE>();
+    case 4: return kernel_ptr<4, MODE, EXT>();
+    case 8: return kernel_ptr<8, MODE, EXT>();
+    case 16: return kernel_ptr<16, MODE, EXT>();
+    case 32: return kernel_ptr<32, MODE, EXT>();
     default: return nullptr;
     }
 }
 
-static void* select_kernel(int tpa, int mode)
+// variant = kernel mode (0 matrix, 1 SPM in global memory, 2 SPM resident),
+// plus kExtVariant for the SPM modes with the extended lists
+static void* select_kernel(int tpa, int variant)
 {
-    switch (mode) {
-    case 0: return select_tpa<0>(tpa);
-    case 1: return select_tpa<1>(tpa);
-    case 2: return select_tpa<2>(tpa);
+    switch (variant) {
+    case 0: return select_tpa<0, false>(tpa);
+    case 1: return select_tpa<1, false>(tpa);
+    case 2: return select_tpa<2, false>(tpa);
+    case 1 + kExtVariant: return select_tpa<1, true>(tpa);
+    case 2 + kExtVariant: return select_tpa<2, true>(tpa);
     default: return nullptr;
     }
 }

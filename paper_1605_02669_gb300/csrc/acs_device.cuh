@@ -66,6 +66,15 @@ __device__ __forceinline__ float global_rule(float t, float delta, float rho)
     return __fadd_rn(t, __fmul_rn(rho, __fsub_rn(delta, t)));
 }
 
+// Full-scan key of node j: (product bits, node) packed so that the larger
+// product wins and, among equal products, the lower node index
+// (non-negative floats order like their bit patterns). Nonzero for j >= 0.
+__device__ __forceinline__ unsigned long long pack_pj(float p, int j)
+{
+    return ((unsigned long long)__float_as_uint(p) << 32) |
+           (unsigned long long)(0xffffffffu - (uint32_t)j);
+}
+
 __device__ __forceinline__ uint32_t hash32(uint32_t k)
 {
     return k * 2654435761u;

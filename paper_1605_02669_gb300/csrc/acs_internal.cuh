@@ -58,16 +58,23 @@ struct ConstructArgs {
     int32_t mc;               // ants per CTA of a cluster = ceil(m / cluster size)
     int32_t nrec;             // SPM records per CTA in shared memory (0 = global)
     int32_t skip_default;     // SPM: a local update of an absent edge inserts nothing
+    const int32_t* ext;       // SPM: per node the kExtList nodes with the largest full-scan
+                              // keys of an absent trail, best first, -1 padded; or null
     int32_t* sched;           // next-instance counter (zeroed before each launch) when the
                               // batch has more instances than resident clusters; null =
                               // cluster k takes instances k, k + clusters, ...
 };
 
+// Length of the SPM's extended neighbour lists (rows of ConstructArgs::ext).
+constexpr int kExtList = 256;
+// Added to an SPM kernel mode to select the variant that uses those lists.
+constexpr int kExtVariant = 3;
+
 // Shared-memory carve of the construct kernel; the same arithmetic runs on
 // the host (to size the launch) and on the device (to place the arrays).
 // mc = ants owned by one CTA of the cluster, m = ants of the instance.
 struct SmemLayout {
-    uint32_t P, cur, start, nxt, tsel, len, pedge, qant, qc, qpart, eqal, gkey, gu, gv, grep, gcnt,
+    uint32_t P, cur, start, nxt, tsel, len, pedge, qant, qc, qpart, xj, eqal, gkey, gu, gv, grep, gcnt,
         ev0, ev1, misc, ridx, rval, rtail, vis, xy, total;
 };
 
@@ -91,6 +98,7 @@ __host__ __device__ inline SmemLayout smem_layout(int m, int mc, int nrec, int s
     L.qant = o;  o = align16(o + 4u * mc);
     L.qc = o;    o = align16(o + 4u * mc);
     L.qpart = o; o = align16(o + 8u * mc);
+    L.xj = o;    o = align16(o + 4u * mc);
     L.eqal = o;  o = align16(o + 4u * m);
     L.gkey = o;  o = align16(o + 4u * m);
     L.gu = o;    o = align16(o + 4u * m);

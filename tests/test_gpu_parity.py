@@ -115,6 +115,22 @@ def test_edge_cases(oracle_mod, case, memory, slots):
         assert_same_state(gpu, ref, memory)
 
 
+@pytest.mark.parametrize("beta", [0, 2, 8])
+def test_spm_extended_list_ties(oracle_mod, beta):
+    # The SPM resolves most empty candidate sets from a per-node list sorted
+    # by the full scan's key. Duplicated points (d = 0 weighs like d = 1),
+    # beta 0 (every heuristic equal: the lowest index wins) and beta 8
+    # (products underflow to denormals and to zero) make many equal keys; with
+    # n - 1 > 256 and two candidates, both the list and the full scan run.
+    base = instances.uniform(420, side=400, seed=beta + 3)
+    xy = np.concatenate([base, base[:120]]).astype(np.int32)
+    gpu, ref = _pair(xy, memory=1, m=48, cl=2, spm_slots=4, beta=beta, seed=9)
+    for _ in range(3):
+        gpu.run(1)
+        ref.run(1)
+        assert_same_state(gpu, ref, 1)
+
+
 @pytest.mark.parametrize("memory", [0, 1])
 def test_m128_n1002_clustered(oracle_mod, memory):
     xy = instances.clustered(1002, seed=2)
