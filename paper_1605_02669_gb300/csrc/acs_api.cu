@@ -438,8 +438,19 @@ cudaError_t configure(acs_ctx* c, int tpa, int csize)
     // the SPM variant with the extended lists when some instance's full scan
     // would deal each warp of a CTA more than two 128-node items (the kernel
     // applies the same test per instance)
-    const bool ext = spm && c->d_ext && ((c->max_n + 127) >> 7) > 2 * (block >> 5);
+    const bool ext = spm && ((c->max_n + 127) >> 7) > 2 * (block >> 5);
     const int variant = mode + (ext ? kExtVariant : 0);
+    if (ext && !c->d_ext) {
+        // built once, the first time a launch shape uses them (tau0 is in the
+        // descriptors by now); stream-ordered before any launch that reads them
+        size_t rows = 0;
+        for (int b = 0; b < c->B; ++b) rows += (size_t)c->n[b];
+        ACS_TRY(dalloc(c, &c->d_ext, (size_t)kExtList * rows));
+        ext_list_kernel<<<dim3(std::min(c->max_n, 4096), c->B), 256, 0, c->stream>>>(c->d_desc, c->d_xy,
+                                                                                  c->d_ext, c->p.beta);
+        ACS_TRY(cudaGetLastError());
+        c->args.ext = c->d_ext;
+    }
     ACS_TRY(prepare_construct(tpa, variant, L.total));
     const int ncl = construct_occupancy(tpa, variant, block, L.total, csize);
     if (ncl < 1) return cudaErrorInvalidConfiguration;
@@ -592,7 +603,6 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     if (c->p.memory == ACS_MEM_SPM) {
         ACS_TRY(dalloc(c, &c->d_spm_idx, tau_total));
         ACS_TRY(dalloc(c, &c->d_spm_tail, (size_t)total_n));
-        ACS_TRY(dalloc(c, &c->d_ext, (size_t)kExtList * total_n));
     }
     ACS_TRY(dalloc(c, &c->d_tours, tour_total));
     ACS_TRY(dalloc(c, &c->d_lens, (size_t)B * m));
@@ -628,11 +638,6 @@ cudaError_t build(acs_ctx* c, const int32_t* coords, const int64_t* offsets)
     const size_t vis_bytes = sizeof(uint32_t) * ((c->max_n + 31) / 32);
     nn_tour_kernel<<<B, 32, vis_bytes, st>>>(c->d_desc, c->d_xy, c->d_nn, c->d_Lnn);
     ACS_TRY(cudaGetLastError());
-    if (c->d_ext) {   // needs tau0, which the tour kernel stored in the descriptors
-        ext_list_kernel<<<dim3(std::min(c->max_n, 4096), B), 256, 0, st>>>(c->d_desc, c->d_xy, c->d_ext,
-                                                                           c->p.beta);
-        ACS_TRY(cudaGetLastError());
-    }
     dim3 ig(256, B);
     if (c->d_hw) {
         hw_kernel<<<dim3(1024, B), 256, 0, st>>>(c->d_desc, c->d_xy, c->d_hw, c->p.beta);

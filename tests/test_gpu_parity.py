@@ -115,20 +115,34 @@ def test_edge_cases(oracle_mod, case, memory, slots):
         assert_same_state(gpu, ref, memory)
 
 
+@pytest.mark.parametrize("tpa,m,n0,ndup", [(4, 16, 600, 120), (32, 4, 900, 200)])
 @pytest.mark.parametrize("beta", [0, 2, 8])
-def test_spm_extended_list_ties(oracle_mod, beta):
-    # The SPM resolves most empty candidate sets from a per-node list sorted
-    # by the full scan's key. Duplicated points (d = 0 weighs like d = 1),
-    # beta 0 (every heuristic equal: the lowest index wins) and beta 8
-    # (products underflow to denormals and to zero) make many equal keys; with
-    # n - 1 > 256 and two candidates, both the list and the full scan run.
-    base = instances.uniform(420, side=400, seed=beta + 3)
-    xy = np.concatenate([base, base[:120]]).astype(np.int32)
-    gpu, ref = _pair(xy, memory=1, m=48, cl=2, spm_slots=4, beta=beta, seed=9)
-    for _ in range(3):
-        gpu.run(1)
-        ref.run(1)
-        assert_same_state(gpu, ref, 1)
+def test_spm_extended_list_ties(oracle_mod, beta, tpa, m, n0, ndup):
+    # The SPM settles empty candidate sets from a per-node list sorted by the
+    # full scan's key when a scan would be long. 160 instances on one-CTA
+    # clusters (more clusters than SMs, so small CTAs: m x lanes per ant = 64
+    # or 128 threads, and a scan of n0 + ndup nodes would deal each warp more
+    # than two items) select that path, with 4 and with 32 lanes per ant. Duplicated points (d = 0 weighs like d = 1), beta 0
+    # (every heuristic equal: the lowest index wins) and beta 8 (products
+    # underflow to denormals and to zero) make many equal keys; two candidates
+    # make empty candidate sets frequent, so the list path and, once all 256
+    # listed nodes are visited, the full scan both run.
+    B = 160
+    parts = []
+    for b in range(B):
+        base = instances.uniform(n0, side=700, seed=beta + 3, stream=b)
+        parts.append(np.concatenate([base, base[:ndup]]))
+    xy = np.concatenate(parts).astype(np.int32)
+    off = np.arange(B + 1, dtype=np.int64) * (n0 + ndup)
+    kw = dict(memory=1, m=m, cl=2, spm_slots=4, beta=beta, seed=9)
+    gpu = acs.Colony(xy, acs.params(**kw), offsets=off)
+    gpu.set_cluster_size(1)
+    gpu.set_threads_per_ant(tpa)
+    gpu.run(2)
+    for b in (0, 1, 37, 80, 121, 159):
+        ref = oracle.Colony(xy[off[b]:off[b + 1]], oracle.make_params(**kw), instance=b)
+        ref.run(2)
+        assert_same_state(gpu, ref, 1, b)
 
 
 @pytest.mark.parametrize("memory", [0, 1])
