@@ -35,9 +35,9 @@
  *   - Every call returns an acs_status and never aborts. On ACS_EINVAL /
  *     ACS_ENOMEM the context is unchanged. After ACS_ECUDA or ACS_ETIMEOUT
  *     the context is poisoned: later calls on it return ACS_ESTATE.
- *   - Limits: 3 <= n <= 65536 per instance; coordinates in [0, 2^20);
- *     1 <= m <= 1024; 1 <= cl <= 32 (clamped to n-1); 0 <= beta <= 8;
- *     1 <= spm_slots <= 32.
+ *   - Limits: 3 <= n <= 65536 per instance; 1 <= B <= 65535 instances per
+ *     context; coordinates in [0, 2^20); 1 <= m <= 1024; 1 <= cl <= 32
+ *     (clamped to n-1); 0 <= beta <= 8; 1 <= spm_slots <= 32.
  *   - A context is not thread-safe; use one host thread per context.
  */
 #ifndef ACS_H

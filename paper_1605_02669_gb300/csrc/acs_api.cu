@@ -723,7 +723,8 @@ acs_status acs_create_batch_ids(const int32_t* coords, const int64_t* offsets,
 {
     if (!out) return ACS_EINVAL;
     *out = nullptr;
-    if (!coords || !offsets || B < 1) return ACS_EINVAL;
+    // B is a grid dimension of the set-up kernels (one grid row per instance)
+    if (!coords || !offsets || B < 1 || B > 65535) return ACS_EINVAL;
     acs_status vs = validate_params(p);
     if (vs != ACS_OK) return vs;
     if (offsets[0] != 0) return ACS_EINVAL;

@@ -90,6 +90,10 @@ def test_bad_coords_and_sizes_rejected_on_host(lib):
     assert lib.acs_create_batch(xy.ctypes.data_as(ctypes.c_void_p),
                                 off.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(p),
                                 ctypes.byref(h)) == acs.ACS_EINVAL
+    # more instances than a grid dimension holds: rejected before any device work
+    assert lib.acs_create_batch(xy.ctypes.data_as(ctypes.c_void_p),
+                                off.ctypes.data_as(ctypes.c_void_p), 65536, ctypes.byref(p),
+                                ctypes.byref(h)) == acs.ACS_EINVAL
 
 
 def test_null_context_calls(lib):
